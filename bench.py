@@ -1,0 +1,412 @@
+"""Benchmark of the matrix-free p-Laplacian Jacobian action and Newton-CG solve on one GB300.
+
+Workload: 3D p-Laplacian p=3 on a 64^3 hex lattice with seeded jitter, order 3 (7,189,057 DOFs),
+4^3 Gauss points per element, linearised at the seeded smooth state.  One timed step is one
+partially assembled Jacobian action y = J(u) v in FP32 (the operator the mixed-precision CG
+applies); the FP64 action, the FP64 residual and the full Newton-CG solves (FP64 and mixed
+precision, to 1e-8 relative residual) are measured in the same run and reported beside it.
+
+Prints one JSON line.  ``--impl reference`` times the oracle (plain FP64 C on the host cores) on
+a bounded sample of the same workload instead.  Under torchrun every rank runs an independent
+replica on its own GPU (the single-GPU problem does not exchange data); timing is the max over
+ranks and the value sums the work of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian action GDOF/s; Newton solve time to 1e-8 rel residual, FP64 vs mixed"
+WORKLOAD = "3d_p3_k3_64"
+
+
+# ------------------------------------------------------------------------------------------------
+# distributed helpers (host logic; tested on CPU with gloo)
+# ------------------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and getattr(device, "type", "cpu") == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(units_per_rank: float, seconds_per_rank: float, world: int, device=None) -> tuple[float, float]:
+    """Whole-job throughput: units of all ranks / max time over ranks (weak scaling)."""
+    t = max_over_ranks(seconds_per_rank, device)
+    return units_per_rank * world / t, t
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ------------------------------------------------------------------------------------------------
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def jv_algorithmic_bytes(n_l: int, n_e: int, nq_per_elem: int, nl_per_elem: int, word: int) -> int:
+    """Bytes a partially assembled J v must move: read v and write y (N_L words each), read the
+    6 symmetric tangent entries per quadrature point, read the element index (4 B per E-vector
+    entry)."""
+    return 2 * word * n_l + 6 * word * n_e * nq_per_elem + 4 * n_e * nl_per_elem
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("element_kernels.cuh", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2506_00746_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str) -> tuple[float | None, str | None]:
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    d = json.load(open(path))
+    e = d.get(kernel)
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None, None
+    return float(e["dram_bytes_per_launch"]), e.get("summary")
+
+
+# ------------------------------------------------------------------------------------------------
+# the GPU arm
+# ------------------------------------------------------------------------------------------------
+def run_gpu(args) -> dict | None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import inputs as I
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+    w = I.WORKLOADS[args.workload]
+    V = I.lattice_vertices(w.dim, w.n, seed=w.mesh_seed)
+    op = Operator(w.dim, w.n, w.order, V, p=w.p, eps=w.eps)
+    nl, ne = op.n_dofs, op.n_elements
+    nq = (w.order + 1) ** w.dim
+    u0 = torch.from_numpy(I.smooth_field(w.dim, w.n, w.order, seed=w.state_seed)).to(dev)
+    v64 = torch.from_numpy(I.uniform_vector(nl, seed=w.dir_seed)).to(dev)
+    v32 = v64.float()
+    y32 = torch.empty_like(v32)
+    y64 = torch.empty_like(v64)
+    op.linearize(u0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = op.launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(dev)
+        return e0.elapsed_time(e1) / 1e3, op.launch_count() - l0
+
+    # ---- headline: FP32 Jacobian action, device-resident inputs ----
+    jv32 = lambda: op.jacobian_action(v32, precision=32, out=y32)
+    clk = ClockSampler(local).start()
+    t_dev, launches = timed(jv32, args.steps, args.warmup)
+    clocks = clk.stop()
+    value, t_max = aggregate(nl * args.steps / 1e9, t_dev, world, dev)
+
+    # ---- per-kernel durations over the same kind of timed region (library CUDA events) ----
+    op.prof_enable(True)
+    op.prof_reset()
+    for _ in range(args.steps):
+        jv32()
+    prof = op.prof_read()
+    op.prof_enable(False)
+    main_n, main_ms = prof.get("jv_pa_f32", (1, float("nan")))
+    fix_n, fix_ms = prof.get("fixup", (0, 0.0))
+    t_main = main_ms / 1e3 / max(main_n, 1)
+    t_fix = fix_ms / 1e3 / max(fix_n, 1) if fix_n else 0.0
+
+    # ---- other operators of the path ----
+    jv64 = lambda: op.jacobian_action(v64, precision=64, out=y64)
+    t64, _ = timed(jv64, max(3, args.steps // 20), 2)
+    n64 = max(3, args.steps // 20)
+    jvcg = lambda: op.jacobian_action(v64, precision=-32, out=y64)
+    tcg, _ = timed(jvcg, args.steps, 3)
+    r = torch.empty_like(u0)
+    res = lambda: op.residual(u0, out=r)
+    nres = max(3, args.steps // 20)
+    tres, _ = timed(res, nres, 2)
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region) ----
+    vh = v32.cpu().pin_memory()
+    yh = torch.empty_like(vh).pin_memory()
+    for _ in range(3):
+        op.jacobian_action_host(vh, yh, precision=32)
+    torch.cuda.synchronize()
+    barrier(dev)
+    ne2e = max(5, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        op.jacobian_action_host(vh, yh, precision=32)
+    t_e2e = time.perf_counter() - t0
+    e2e_value, _ = aggregate(nl * ne2e / 1e9, t_e2e, world, dev)
+
+    # ---- Newton solves: FP64 and mixed precision to 1e-8 ----
+    newton = {}
+    if not args.no_newton:
+        for name, prec in (("mixed", 32), ("fp64", 64)):
+            u = u0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = op.newton_solve(u, rtol=1e-8, inner_precision=prec, max_newton=args.max_newton,
+                                  raise_on_error=False)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            newton[name] = {"time_s": round(max_over_ranks(wall, dev), 4), "status": rep["status"],
+                            "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
+                            "rel_residual": rep["rel"], "cg_time_s": round(rep["cg_ms"] / 1e3, 4),
+                            "kernel_launches": rep["launches"]}
+        if "fp64" in newton and "mixed" in newton:
+            newton["speedup_mixed_vs_fp64"] = round(newton["fp64"]["time_s"] / newton["mixed"]["time_s"], 3)
+
+    if rank != 0:
+        op.close()
+        return None
+
+    peaks = measured_peaks()
+    bytes_alg = jv_algorithmic_bytes(nl, ne, nq, nq, 4)
+    achieved = bytes_alg / t_main / 1e9
+    traffic, traffic_src = profiled_traffic("k_jv_pa<3,4,float,float>")
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "GDOF/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps * 1e3, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded jittered lattice, seeded smooth state, seeded U[-1,1] direction)",
+        "config": {"workload": f"{args.workload}: 3D p-Laplacian p=3, 64^3 hex, order 3, 4^3 Gauss points, "
+                               f"{nl} DOFs; step = one FP32 partially assembled J(u) v",
+                   "n_dofs": nl, "n_elements": ne, "order": w.order, "p": w.p,
+                   "l2": "inputs larger than L2 (FP32 tangent %.0f MB + index/vectors)" % (6 * 4 * ne * nq / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU", "tile": None},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                     "kernel": "k_jv_pa<3,4,float,float>", "peak_source": peaks["source"],
+                     "algorithmic_bytes_per_launch": bytes_alg,
+                     "kernel_ms": round(t_main * 1e3, 5), "fixup_ms": round(t_fix * 1e3, 5),
+                     "traffic_summary": traffic_src},
+        "e2e": {"value": round(e2e_value, 4), "unit": "GDOF/s", "h2d_bytes_per_step": 4 * nl,
+                "d2h_bytes_per_step": 4 * nl},
+        "jv_f64_gdofs": round(nl * n64 / t64 / 1e9, 4),
+        "jv_cg_mixed_gdofs": round(nl * args.steps / tcg / 1e9, 4),
+        "residual_f64_gdofs": round(nl * nres / tres / 1e9, 4),
+        "newton": newton,
+        "kernel_ms": {k: round(ms / max(n, 1), 5) for k, (n, ms) in prof.items()},
+    }
+    op.close()
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline / reference arm)
+# ------------------------------------------------------------------------------------------------
+def cpu_baseline(workload: str, budget_s: float = 12.0) -> dict:
+    """Oracle J v (element by element, FP64, OpenMP over element colours) on a bounded sample of
+    the elements of the workload, scaled to GDOF/s of a whole action."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2506_00746_gb300 import inputs as I
+    w = I.WORKLOADS[workload]
+    V = I.lattice_vertices(w.dim, w.n, seed=w.mesh_seed)
+    P = O.Problem(w.dim, w.n, w.order, V, p=w.p, eps=w.eps)
+    u = I.smooth_field(w.dim, w.n, w.order, seed=w.state_seed)
+    v = I.uniform_vector(P.n_dofs, seed=w.dir_seed)
+    cores = O.set_threads(os.cpu_count() or 1)
+    y = np.zeros(P.n_dofs)
+    m = max(1, P.n_elems // 512)
+    t0 = time.perf_counter()
+    O.jv_partial(P, u, v, 0, m, y)
+    dt = time.perf_counter() - t0
+    m = int(min(P.n_elems, max(m, m * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    O.jv_partial(P, u, v, 0, m, y)
+    dt = time.perf_counter() - t0
+    value = P.n_dofs * (m / P.n_elems) / dt / 1e9
+    return {"value": round(value, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"element-by-element FP64 J(u) v over the first {m} of {P.n_elems} elements "
+                      f"({dt:.1f} s), scaled by the element fraction"}
+
+
+def run_reference(args) -> dict | None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import oracle as O
+    from paper_2506_00746_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    V = I.lattice_vertices(w.dim, w.n, seed=w.mesh_seed)
+    P = O.Problem(w.dim, w.n, w.order, V, p=w.p, eps=w.eps)
+    u = I.smooth_field(w.dim, w.n, w.order, seed=w.state_seed)
+    v = I.uniform_vector(P.n_dofs, seed=w.dir_seed)
+    cores = O.set_threads(os.cpu_count() or 1)
+    y = np.zeros(P.n_dofs)
+    # each step is the oracle J v over a bounded element sample, sized for ~1.5 s
+    m = max(1, P.n_elems // 1024)
+    t0 = time.perf_counter()
+    O.jv_partial(P, u, v, 0, m, y)
+    dt = time.perf_counter() - t0
+    m = int(min(P.n_elems, max(m, m * 1.5 / max(dt, 1e-6))))
+    for _ in range(args.warmup):
+        O.jv_partial(P, u, v, 0, m, y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.jv_partial(P, u, v, 0, m, y)
+    dt = time.perf_counter() - t0
+    value = P.n_dofs * (m / P.n_elems) * args.steps / dt / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "GDOF/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: same workload as the GPU arm; each step is the oracle "
+                                   f"J(u) v over {m} of {P.n_elems} elements, scaled by the element fraction"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {m} of {P.n_elems} elements per step"},
+            "e2e": {"value": round(value, 6), "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-newton", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--max-newton", type=int, default=50)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * feod.h -- C ABI of the GB300 (sm_103a) matrix-free finite element operator library.
+ *
+ * The library applies the finite element operator decomposition A = P^T G^T B^T D B G P
+ * (Fig. 1 and Eq. 1) of the steady p-Laplacian  -div(kappa(|grad u|) grad u) = f,
+ * kappa = kappa_rho(rho_e) (eps^2 + |grad u|^2)^((p-2)/2), and its exact Jacobian
+ * J(u) = P^T G^T B^T J_D(u_q) B G P (Eq. 2), where the pointwise operator D is differentiated
+ * at each quadrature point with forward-mode dual numbers.  On top of these it runs a
+ * matrix-free Newton-CG solve and the adjoint design gradient (the adjoint loads of the
+ * design-sensitivity discussion that follows Eq. 3).
+ *
+ * Discretisation: structured lattice of n^dim elements on the unit box (dim = 2 or 3) with
+ * caller-given (jittered) vertices and a multilinear geometry map per element; continuous
+ * Lagrange basis of order k = 1..6 on Gauss-Lobatto-Legendre nodes; (k+1)^dim Gauss-Legendre
+ * points per element.  DOFs form the lattice (k n + 1)^dim, numbered lexicographically with x
+ * fastest; elements are numbered ex + n (ey + n ez).  Essential (Dirichlet) DOFs are all DOFs on
+ * the boundary of the box.  On one GPU the subdomain restriction P is the identity plus this
+ * Dirichlet elimination:
+ *   - R(u) = A(u) - F with R_i = 0 on essential DOFs (u carries the boundary values);
+ *   - J(u) v treats essential entries of v as zero and returns y_i = v_i on essential DOFs,
+ *     so J is symmetric positive (semi)definite.
+ *
+ * Conventions for every call:
+ *   - Vector arguments are DEVICE pointers owned by the caller, of length N_L (number of DOFs)
+ *     unless stated otherwise; the library never frees or retains them beyond the call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are stream-ordered and
+ *     asynchronous unless stated otherwise; the caller keeps inputs alive until the stream work
+ *     completes.
+ *   - Every call returns an fe_status and never aborts or traps; the message of the last non-OK
+ *     status of a context is returned by fe_last_error().
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef FEOD_H
+#define FEOD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_ctx fe_ctx;
+
+typedef enum {
+    FE_OK = 0,
+    FE_ERR_ARG = 1,            /* invalid argument (null pointer, size, range)               */
+    FE_ERR_MESH = 2,           /* det J <= 0 at some quadrature point (inverted element)      */
+    FE_ERR_CUDA = 3,           /* a CUDA runtime call failed                                  */
+    FE_ERR_OOM = 4,            /* device or host allocation failed                           */
+    FE_ERR_UNSUPPORTED = 5,    /* order / quadrature / size outside what is built            */
+    FE_ERR_NAN = 6,            /* a NaN or Inf appeared in a norm                            */
+    FE_ERR_NOT_CONVERGED = 7,  /* Newton or CG reached its iteration limit                   */
+    FE_ERR_BREAKDOWN = 8,      /* CG found p^T J p <= 0 or the line search failed             */
+    FE_ERR_STATE = 9           /* call out of order (e.g. cached Jacobian requested before
+                                  fe_linearize)                                               */
+} fe_status;
+
+/* Structured lattice mesh.  `vertices` is a HOST array [(n+1)^dim][dim], lexicographic with x
+ * fastest; it is copied during fe_setup. */
+typedef struct {
+    int dim;                   /* 2 or 3                                                      */
+    int n;                     /* elements per direction, >= 1                                */
+    const double *vertices;
+} fe_mesh;
+
+/* The pointwise law and the load.  kappa_rho(rho) = kappa_eps + rho^kappa_q multiplies the flux
+ * when `rho` is given (one HOST value per element, copied), else kappa_rho = 1. */
+typedef struct {
+    double p;                  /* exponent; p >= 2, or p > 1 with eps > 0                     */
+    double eps;                /* regularisation of |grad u|^2 (0 = the plain p-Laplacian)     */
+    int f_kind;                /* 0: f = f_const; 1: manufactured source of u* = exp(x+y/2+z/3) */
+    double f_const;
+    const double *rho;         /* host, [n^dim] or NULL                                       */
+    double kappa_eps;
+    double kappa_q;
+} fe_problem;
+
+/* Launch-shape options (fe_setup picks them from the built-in tuning table). */
+typedef struct {
+    int tile;                  /* elements per tile edge: one CTA owns tile^dim elements;
+                                  0 = tuned default                                           */
+} fe_setup_opts;
+
+/* fe_setup: build a context for the mesh, order k (1..6) and quadrature q1d (0 or k+1 Gauss
+ * points per direction).  Copies the mesh and design field to the device, builds the element
+ * restriction G as explicit index arrays (tile slot codes and the transposed halo index that
+ * makes G^T deterministic without atomics), and evaluates the geometric factors at every
+ * quadrature point (w det J J^{-1}J^{-T}, 1/(w det J), w det J f).  Fig. 1 / the decomposition
+ * paragraph: P, G and B are linear and topological and set up once, outside differentiation.
+ * Synchronises the current device.  Errors: FE_ERR_ARG, FE_ERR_MESH (det J <= 0),
+ * FE_ERR_UNSUPPORTED (order, q1d, or more than 2^30-1 DOFs), FE_ERR_OOM, FE_ERR_CUDA.
+ * On success *out owns all device memory it allocated; release with fe_destroy. */
+fe_status fe_setup(const fe_mesh *mesh, int order, int q1d, const fe_problem *prob, fe_ctx **out);
+fe_status fe_setup_ex(const fe_mesh *mesh, int order, int q1d, const fe_problem *prob,
+                      const fe_setup_opts *opts, fe_ctx **out);
+
+/* Number of DOFs N_L, free (non-essential) DOFs and elements. */
+fe_status fe_num_dofs(const fe_ctx *ctx, int64_t *n_l, int64_t *n_free);
+fe_status fe_num_elements(const fe_ctx *ctx, int64_t *n_e);
+
+/* fe_residual: r = R(u) = P^T G^T B^T D(B G P u) - F (Eq. 1 minus the load), FP64, essential
+ * entries zero.  u, r: device double[N_L]; may not alias. */
+fe_status fe_residual(fe_ctx *ctx, const double *u, double *r, void *stream);
+
+/* fe_linearize: evaluate J_D at every quadrature point of u (Eq. 2) with 3 (2 in 2D) dual
+ * directions and store it inside the context (partial assembly: FP64 and its FP32 rounding,
+ * d(d+1)/2 symmetric entries per point), plus the Jacobi diagonal of J.  u: device double[N_L]. */
+fe_status fe_linearize(fe_ctx *ctx, const double *u, void *stream);
+
+/* fe_jacobian_action: y = J(u) v (Eq. 2).
+ *   u == NULL : uses the quadrature-point Jacobian cached by the last fe_linearize (partial
+ *               assembly); FE_ERR_STATE if there is none.
+ *   u != NULL : stateless: recomputes J_D(u_q) . (B G P v) with one dual direction seeded by the
+ *               gradient of v, nothing cached.
+ *   precision : 64 -> v, y are double[N_L] and all arithmetic is FP64;
+ *               32 -> v, y are float[N_L], FP32 arithmetic and accumulation (the FP32 rounding of
+ *                     the FP64 tangent when cached);
+ *               -32 -> v, y are double[N_L] but the action is computed exactly as for 32 (the
+ *                     inner operator of the mixed-precision Newton-CG).
+ * v and y may not alias. */
+fe_status fe_jacobian_action(fe_ctx *ctx, const double *u, const void *v, void *y, int precision,
+                             void *stream);
+
+/* Same as fe_jacobian_action with u == NULL but v_host/y_host are HOST buffers (pinned memory
+ * recommended): copies v to the device, applies J, copies y back, all on `stream`; synchronises
+ * the stream before returning. */
+fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host, int precision,
+                                  void *stream);
+
+/* fe_jacobian_diagonal: diag(J) of the cached linearisation (1 on essential DOFs), FP64. */
+fe_status fe_jacobian_diagonal(fe_ctx *ctx, double *diag, void *stream);
+
+/* fe_load_vector: F_i = int f phi_i with essential entries zero, FP64. */
+fe_status fe_load_vector(fe_ctx *ctx, double *F, void *stream);
+
+/* fe_node_coords: physical coordinates of every DOF, device double[N_L][dim]. */
+fe_status fe_node_coords(fe_ctx *ctx, double *xyz, void *stream);
+
+/* fe_set_design: replace the per-element design field rho (device double[n^dim], copied on the
+ * stream).  Invalidates the cached linearisation. */
+fe_status fe_set_design(fe_ctx *ctx, const double *rho, void *stream);
+
+/* fe_adjoint_vjp: per-element design gradient of the residual contracted with lambda,
+ *   grad_rho[e] = lambda^T dR/drho_e = kappa_rho'(rho_e) int_e kappa(|grad u|) grad u . grad lambda,
+ * obtained by seeding a dual number on rho at each quadrature point (AD local to the quadrature
+ * point; no scatter, element-local reduction).  For the compliance c = F^T u with R(u; rho) = 0,
+ * dc/drho = -grad_rho evaluated at the adjoint solution J lambda = F.  Needs a design field.
+ * u, lambda: device double[N_L]; grad_rho: device double[n^dim] (element order ex fastest). */
+fe_status fe_adjoint_vjp(fe_ctx *ctx, const double *u, const double *lambda, double *grad_rho,
+                         void *stream);
+
+/* Newton-CG options.  Defaults (fe_newton_default_opts): rtol 1e-8, max_newton 50, max_cg 20000,
+ * cg_rtol 1e-4, inner_precision 64, line_search 1, armijo 1e-4, max_halvings 20,
+ * cg_batch 16, use_graph 1. */
+typedef struct {
+    double rtol;               /* stop when ||R(u_k)||_2 <= rtol ||R(u_0)||_2                    */
+    int max_newton;
+    int max_cg;                /* per Newton step                                              */
+    double cg_rtol;            /* inner CG stops when ||r_cg|| <= cg_rtol ||R(u_k)||           */
+    int inner_precision;       /* 64: FP64 J v in CG; 32: FP32 J v (mixed precision)           */
+    int line_search;           /* 1: backtracking on ||R||_2                                   */
+    double armijo;             /* accept alpha when ||R(u+alpha d)|| <= (1-armijo alpha)||R(u)|| */
+    int max_halvings;
+    int cg_batch;              /* CG iterations enqueued between host convergence checks       */
+    int use_graph;             /* 1: replay each CG batch as a captured CUDA graph             */
+} fe_newton_opts;
+
+#define FE_NEWTON_HIST 64
+
+typedef struct {
+    int newton_iters;
+    int cg_iters_total;
+    int line_search_halvings;
+    int status;                /* fe_status of the solve                                       */
+    double r0, r_final;        /* ||R(u_0)||_2, ||R(u_final)||_2                                */
+    double t_total_ms;         /* wall time of the solve (host clock, device synchronised)     */
+    double t_cg_ms;            /* part of it spent in CG                                       */
+    int64_t kernel_launches;   /* kernels this solve launched (graph replays included)         */
+    double r_hist[FE_NEWTON_HIST];  /* ||R|| after each Newton step                            */
+    int cg_hist[FE_NEWTON_HIST];    /* CG iterations of each Newton step                       */
+} fe_newton_report;
+
+fe_status fe_newton_default_opts(fe_newton_opts *opts);
+
+/* newton_solve: solve R(u) = 0 from u_inout (device double[N_L], carrying the boundary values),
+ * overwritten with the solution.  Each step: R and J_D at u (fused, FP64 dual numbers), Jacobi-
+ * preconditioned CG on J d = -R with the partially assembled J (FP64, or FP32 when
+ * inner_precision = 32; dot products, norms and updates always FP64 and deterministic), then a
+ * backtracking line search on ||R||.  Runs on an internal stream after synchronising `stream`;
+ * synchronous (returns after the solve).  report may be NULL. */
+fe_status newton_solve(fe_ctx *ctx, double *u_inout, const fe_newton_opts *opts,
+                       fe_newton_report *report, void *stream);
+
+/* fe_cg_solve: solve J x = b with the cached linearisation (e.g. the adjoint J lambda = F; J is
+ * symmetric), x starting from 0, Jacobi-preconditioned CG to ||r|| <= rtol ||b||; FP64 or FP32
+ * (precision 64 / 32) operator.  Synchronous.  iters may be NULL. */
+fe_status fe_cg_solve(fe_ctx *ctx, const double *b, double *x, double rtol, int max_iter,
+                      int precision, int *iters, void *stream);
+
+/* Profiling: when enabled, every kernel launch is bracketed by CUDA events on its stream.
+ * fe_prof_read synchronises, then returns for kernel name index i (0 <= i < *count) its name,
+ * number of launches and total milliseconds since the last reset. fe_launch_count returns the
+ * number of kernels launched by the context since the last reset (graph replays included). */
+fe_status fe_prof_enable(fe_ctx *ctx, int enable);
+fe_status fe_prof_reset(fe_ctx *ctx);
+fe_status fe_prof_read(fe_ctx *ctx, int i, const char **name, int64_t *launches, double *ms,
+                       int *count);
+fe_status fe_launch_count(const fe_ctx *ctx, int64_t *launches);
+
+/* Device bytes held by the context. */
+fe_status fe_memory_bytes(const fe_ctx *ctx, int64_t *bytes);
+
+void fe_destroy(fe_ctx *ctx);
+const char *fe_last_error(const fe_ctx *ctx);
+const char *fe_status_string(fe_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEOD_H */

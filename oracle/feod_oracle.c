@@ -704,7 +704,7 @@ int orc_load(const orc_problem *P, double *F)
     return rc;
 }
 
-/* Design gradient of the residual contracted with lambda, per element:
+/* Design gradient of the residual contracted with lambda (essential entries of lambda ignored), per element:
  *   g_e = lambda_e^T dr_e/drho_e = kappa_rho'(rho_e) int_e kappa(|grad u|) grad u . grad lambda,
  * kappa_rho'(rho) = kappa_q rho^(kappa_q - 1).  (Adjoint load, local to quadrature points.) */
 int orc_adjoint_grad(const orc_problem *P, const double *u, const double *lam, double *grad)
@@ -721,7 +721,11 @@ int orc_adjoint_grad(const orc_problem *P, const double *u, const double *lam, d
     qpoint Q = { {0}, 0, W.grad, W.val };
     for (int64_t e = 0; e < NE && !rc; ++e) {
         elem_dofs(P, R, e, W.dofs);
-        for (int l = 0; l < nl; ++l) { W.ue[l] = u[W.dofs[l]]; W.ve[l] = lam[W.dofs[l]]; }
+        /* essential rows of R are identically zero, so lambda's essential entries drop out */
+        for (int l = 0; l < nl; ++l) {
+            W.ue[l] = u[W.dofs[l]];
+            W.ve[l] = is_essential(P, W.dofs[l]) ? 0.0 : lam[W.dofs[l]];
+        }
         double dkr = P->kappa_q * pow(P->rho[e], P->kappa_q - 1.0);
         double acc = 0.0;
         for (int q = 0; q < R->nq; ++q) {

@@ -1,0 +1,225 @@
+"""GB300-native matrix-free finite element operator decomposition with quadrature-point AD.
+
+The operator A = P^T G^T B^T D B G P of the steady p-Laplacian (Fig. 1, Eq. 1), its exact
+Jacobian J(u) = P^T G^T B^T J_D(u_q) B G P with J_D from forward-mode dual numbers (Eq. 2), a
+matrix-free Newton-CG solve and the adjoint design gradient all run in the CUDA library
+``libfeod.so`` (include/feod.h).  This package is its thin binding: ``abi`` has the C entry
+points under their own names, ``Operator`` wraps one context with torch tensors for device memory
+and streams, ``ComplianceFn`` exposes the design gradient to torch autograd.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import abi, inputs
+from .abi import FeodError
+
+__all__ = ["Operator", "ComplianceFn", "FeodError", "abi", "inputs", "build_library"]
+
+
+def build_library(force: bool = False, verbose: bool = False) -> str:
+    from .build import build
+    return build(force=force, verbose=verbose)
+
+
+class Operator:
+    """One problem instance on one GPU (a ``fe_ctx``).
+
+    ``vertices``: host array [(n+1)^dim, dim] (x fastest).  ``rho``: optional per-element design
+    field (host array, element order ex fastest), which makes the flux kappa_rho(rho_e) times the
+    p-Laplacian flux with kappa_rho = kappa_eps + rho^kappa_q.
+    """
+
+    def __init__(self, dim: int, n: int, order: int, vertices, p: float = 3.0, eps: float = 0.0,
+                 f_kind: int = 0, f_const: float = 1.0, rho=None, kappa_eps: float = 1e-3,
+                 kappa_q: float = 3.0, q1d: int = 0, tile: int = 0):
+        import ctypes
+
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Operator needs a CUDA device: the library has no CPU path")
+        self._vert = np.ascontiguousarray(vertices, dtype=np.float64)
+        self._rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+        mesh = abi.fe_mesh(dim, n, self._vert.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        prob = abi.fe_problem(p, eps, f_kind, f_const,
+                              None if self._rho is None else self._rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              kappa_eps, kappa_q)
+        opts = abi.fe_setup_opts(tile) if tile else None
+        self.ctx = abi.fe_setup(mesh, order, q1d, prob, opts)
+        self.dim, self.n, self.order, self.p = dim, n, order, p
+        self.n_dofs, self.n_free = abi.fe_num_dofs(self.ctx)
+        self.n_elements = abi.fe_num_elements(self.ctx)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    # -- helpers ----------------------------------------------------------------------------
+    def _vec(self, dtype=None, n=None):
+        import torch
+        return torch.empty(self.n_dofs if n is None else n, dtype=dtype or torch.float64, device=self.device)
+
+    def _chk(self, t, dtype, n=None, name="vector"):
+        import torch
+        n = self.n_dofs if n is None else n
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+                and t.numel() == n):
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of {n} entries")
+        return t
+
+    # -- operators --------------------------------------------------------------------------
+    def residual(self, u, out=None, stream=None):
+        import torch
+        self._chk(u, torch.float64, name="u")
+        r = out if out is not None else self._vec()
+        abi.fe_residual(self.ctx, u, r, stream)
+        return r
+
+    def linearize(self, u, stream=None):
+        import torch
+        abi.fe_linearize(self.ctx, self._chk(u, torch.float64, name="u"), stream)
+
+    def jacobian_action(self, v, u=None, precision: int = 64, out=None, stream=None):
+        """J(u) v: cached linearisation when u is None, else stateless (dual seeded by grad v).
+
+        precision 64 (double v/y), 32 (float v/y, FP32 arithmetic) or -32 (double v/y, FP32
+        arithmetic)."""
+        import torch
+        io = torch.float32 if precision == 32 else torch.float64
+        self._chk(v, io, name="v")
+        if u is not None:
+            self._chk(u, torch.float64, name="u")
+        y = out if out is not None else self._vec(io)
+        abi.fe_jacobian_action(self.ctx, u, v, y, precision, stream)
+        return y
+
+    def jacobian_action_host(self, v_host, y_host, precision: int = 32, stream=None):
+        abi.fe_jacobian_action_host(self.ctx, v_host, y_host, precision, stream)
+        return y_host
+
+    def jacobian_diagonal(self, stream=None):
+        d = self._vec()
+        abi.fe_jacobian_diagonal(self.ctx, d, stream)
+        return d
+
+    def load_vector(self, stream=None):
+        F = self._vec()
+        abi.fe_load_vector(self.ctx, F, stream)
+        return F
+
+    def node_coords(self, stream=None):
+        import torch
+        xyz = torch.empty((self.n_dofs, self.dim), dtype=torch.float64, device=self.device)
+        abi.fe_node_coords(self.ctx, xyz, stream)
+        return xyz
+
+    def set_design(self, rho, stream=None):
+        import torch
+        abi.fe_set_design(self.ctx, self._chk(rho, torch.float64, self.n_elements, "rho"), stream)
+
+    def adjoint_vjp(self, u, lam, stream=None):
+        import torch
+        g = self._vec(n=self.n_elements)
+        abi.fe_adjoint_vjp(self.ctx, self._chk(u, torch.float64, name="u"),
+                           self._chk(lam, torch.float64, name="lambda"), g, stream)
+        return g
+
+    # -- solvers ----------------------------------------------------------------------------
+    def newton_solve(self, u, rtol: float = 1e-8, inner_precision: int = 64, cg_rtol: float = 1e-4,
+                     max_newton: int = 50, max_cg: int = 20000, line_search: bool = True,
+                     cg_batch: int = 16, use_graph: bool = True, raise_on_error: bool = True, stream=None):
+        """Solve R(u) = 0 in place from u; returns a dict report."""
+        import torch
+        self._chk(u, torch.float64, name="u")
+        o = abi.fe_newton_default_opts()
+        o.rtol, o.inner_precision, o.cg_rtol = rtol, inner_precision, cg_rtol
+        o.max_newton, o.max_cg, o.line_search = max_newton, max_cg, int(line_search)
+        o.cg_batch, o.use_graph = cg_batch, int(use_graph)
+        rep = abi.newton_solve(self.ctx, u, o, stream)
+        out = {"status": abi.STATUS_NAMES.get(rep.status, rep.status), "newton_iters": rep.newton_iters,
+               "cg_iters": rep.cg_iters_total, "halvings": rep.line_search_halvings, "r0": rep.r0,
+               "r_final": rep.r_final, "rel": rep.r_final / rep.r0 if rep.r0 > 0 else 0.0,
+               "time_ms": rep.t_total_ms, "cg_ms": rep.t_cg_ms, "launches": rep.kernel_launches,
+               "r_hist": list(rep.r_hist[:min(rep.newton_iters, abi.FE_NEWTON_HIST)]),
+               "cg_hist": list(rep.cg_hist[:min(rep.newton_iters, abi.FE_NEWTON_HIST)])}
+        if rep.status != abi.FE_OK:
+            out["error"] = getattr(rep, "error", "")
+            if raise_on_error:
+                raise FeodError(rep.status, "newton_solve", out["error"])
+        return out
+
+    def cg_solve(self, b, rtol: float = 1e-10, max_iter: int = 50000, precision: int = 64, stream=None):
+        import torch
+        x = self._vec()
+        it = abi.fe_cg_solve(self.ctx, self._chk(b, torch.float64, name="b"), x, rtol, max_iter, precision, stream)
+        return x, it
+
+    # -- profiling --------------------------------------------------------------------------
+    def prof_enable(self, on: bool = True):
+        abi.fe_prof_enable(self.ctx, on)
+
+    def prof_reset(self):
+        abi.fe_prof_reset(self.ctx)
+
+    def prof_read(self) -> dict:
+        return abi.fe_prof_read(self.ctx)
+
+    def launch_count(self) -> int:
+        return abi.fe_launch_count(self.ctx)
+
+    def memory_bytes(self) -> int:
+        return abi.fe_memory_bytes(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            abi.fe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _compliance_autograd():
+    import torch
+
+    class ComplianceFn(torch.autograd.Function):
+        """c(rho) = F^T u(rho) with R(u; rho) = 0, differentiable in rho by the adjoint method.
+
+        forward: Newton solve from ``u0`` (the converged state is checkpointed, not the Newton
+        history); backward: adjoint CG J(u) lambda = F with the cached linearisation at u, then
+        dc/drho = -lambda^T dR/drho from the quadrature-point dual-number VJP kernel.
+        """
+
+        @staticmethod
+        def forward(ctx, rho, op: "Operator", u0, newton_kw: dict | None = None):
+            op.set_design(rho.detach().contiguous())
+            u = u0.detach().clone()
+            op.newton_solve(u, **(newton_kw or {}))
+            F = op.load_vector()
+            c = torch.dot(F, u)
+            ctx.op = op
+            ctx.save_for_backward(u, F)
+            return c
+
+        @staticmethod
+        def backward(ctx, grad_c):
+            u, F = ctx.saved_tensors
+            op = ctx.op
+            op.linearize(u)
+            lam, _ = op.cg_solve(F, rtol=1e-12)
+            g = -op.adjoint_vjp(u, lam)
+            return grad_c * g, None, None, None
+
+    return ComplianceFn
+
+
+_COMPLIANCE = None
+
+
+def __getattr__(name):
+    global _COMPLIANCE
+    if name == "ComplianceFn":
+        if _COMPLIANCE is None:
+            _COMPLIANCE = _compliance_autograd()
+        return _COMPLIANCE
+    raise AttributeError(name)

@@ -1,0 +1,869 @@
+// api.cu -- the C ABI of include/feod.h: context setup (explicit G index arrays, basis tables,
+// geometry), operator calls, the Jacobi-preconditioned CG and the Newton-CG driver.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "vector_kernels.h"
+
+namespace feod {
+void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &w);
+void gll_nodes(int k, std::vector<double> &x);
+void lagrange_tables(const std::vector<double> &nodes, const std::vector<double> &pts, std::vector<double> &val,
+                     std::vector<double> &der);
+
+// instantiation units (inst_*.cu)
+const OpTable *ops_2d(int d1);
+const OpTable *ops_3d_1();
+const OpTable *ops_3d_2();
+const OpTable *ops_3d_3();
+const OpTable *ops_3d_4();
+const OpTable *ops_3d_5();
+const OpTable *ops_3d_6();
+
+const OpTable *find_ops(int dim, int d1)
+{
+    if (dim == 2) return ops_2d(d1);
+    switch (d1) {
+    case 2: return ops_3d_1();
+    case 3: return ops_3d_2();
+    case 4: return ops_3d_3();
+    case 5: return ops_3d_4();
+    case 6: return ops_3d_5();
+    case 7: return ops_3d_6();
+    default: return nullptr;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// profiling
+// ------------------------------------------------------------------------------------------------
+int prof_name_id(fe_ctx *c, const char *name)
+{
+    for (size_t i = 0; i < c->prof_names.size(); ++i)
+        if (c->prof_names[i] == name) return (int)i;
+    c->prof_names.emplace_back(name);
+    c->prof_count.push_back(0);
+    c->prof_ms.push_back(0.0);
+    return (int)c->prof_names.size() - 1;
+}
+
+static cudaEvent_t take_event(fe_ctx *c)
+{
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(fe_ctx *c, int, cudaStream_t st, cudaEvent_t *a)
+{
+    *a = take_event(c);
+    cudaEventRecord(*a, st);
+}
+
+void prof_end(fe_ctx *c, int id, cudaStream_t st, cudaEvent_t a)
+{
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, st);
+    c->prof_recs.push_back({ id, a, b });
+}
+
+}  // namespace feod
+
+using namespace feod;
+
+// ------------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+fe_status fail(fe_ctx *c, fe_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+fe_status fail(fe_ctx *c, fe_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA, "%s: %s (%s:%d)",   \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+    } while (0)
+
+#define CKLAUNCH()                                                                                        \
+    do {                                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                                              \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail(c, FE_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__,     \
+                        __LINE__);                                                                        \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(fe_ctx *c, T **p, size_t count)
+{
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) c->mem_bytes += (int64_t)bytes;
+    return e;
+}
+
+int64_t ipow64(int64_t b, int e) { int64_t r = 1; while (e-- > 0) r *= b; return r; }
+
+// tuned default tile edge (elements per CTA = T^dim) per (dim, order)
+int default_tile(int dim, int k)
+{
+    if (dim == 3) {
+        static const int t3[7] = { 0, 4, 3, 2, 2, 2, 2 };
+        return t3[k];
+    }
+    static const int t2[7] = { 0, 8, 8, 8, 6, 6, 6 };
+    return t2[k];
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+CgState *cg_state(fe_ctx *c) { return reinterpret_cast<CgState *>(c->w_state); }
+CgState *cg_host(fe_ctx *c) { return reinterpret_cast<CgState *>(c->h_state); }
+
+fe_status ensure_work(fe_ctx *c)
+{
+    if (c->w_r) return FE_OK;
+    const size_t n = (size_t)c->nl;
+    CK(dalloc(c, &c->w_r, n));
+    CK(dalloc(c, &c->w_d, n));
+    CK(dalloc(c, &c->w_trial, n));
+    CK(dalloc(c, &c->w_dinv, n));
+    CK(dalloc(c, &c->w_cx, n));
+    CK(dalloc(c, &c->w_cr, n));
+    CK(dalloc(c, &c->w_cp, n));
+    CK(dalloc(c, &c->w_cq, n));
+    CgState *s = nullptr;
+    CK(dalloc(c, &s, 2));
+    CK(cudaMemset(s, 0, 2 * sizeof(CgState)));
+    c->w_state = s;
+    CK(dalloc(c, &c->w_partial, 3 * RED_BLOCKS));
+    CK(cudaMallocHost(&c->h_state, 2 * sizeof(CgState)));
+    CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    return FE_OK;
+}
+
+fe_status ensure_tangent(fe_ctx *c, bool f64, bool f32)
+{
+    const size_t n = (size_t)c->nepad * c->NS * c->NQ;
+    if (f64 && !c->d_T64) { CK(dalloc(c, &c->d_T64, n)); CK(cudaMemset(c->d_T64, 0, n * sizeof(double))); }
+    if (f32 && !c->d_T32) { CK(dalloc(c, &c->d_T32, n)); CK(cudaMemset(c->d_T32, 0, n * sizeof(float))); }
+    if (!c->d_diag) CK(dalloc(c, &c->d_diag, (size_t)c->nl));
+    return FE_OK;
+}
+
+// deterministic dot product, synchronous on stream st
+fe_status dot_sync(fe_ctx *c, const double *a, const double *b, double *out, cudaStream_t st)
+{
+    CgState *ds = cg_state(c) + 1;
+    {
+        LaunchScope ls(c, "dot", st);
+        k_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, c->nl, c->w_partial + 2 * RED_BLOCKS, &ds->counter, &ds->scalar);
+    }
+    CKLAUNCH();
+    CK(cudaMemcpyAsync(&cg_host(c)[1].scalar, &ds->scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *out = cg_host(c)[1].scalar;
+    return FE_OK;
+}
+
+fe_status apply_jv_cached(fe_ctx *c, const void *v, void *y, int precision, cudaStream_t st)
+{
+    if (precision == 64) {
+        if (!c->lin64) return fail(c, FE_ERR_STATE, "no FP64 linearisation cached (call fe_linearize)");
+        c->ops->jv_pa_64(c, (const double *)v, (double *)y, st);
+    } else if (precision == 32) {
+        if (!c->lin32) return fail(c, FE_ERR_STATE, "no FP32 linearisation cached (call fe_linearize)");
+        c->ops->jv_pa_32(c, (const float *)v, (float *)y, st);
+    } else if (precision == -32) {
+        if (!c->lin32) return fail(c, FE_ERR_STATE, "no FP32 linearisation cached (call fe_linearize)");
+        c->ops->jv_pa_32d(c, (const double *)v, (double *)y, st);
+    } else {
+        return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
+// Enqueue `m` CG iterations (J p, alpha, update, direction); every kernel is a no-op once the
+// device flag `done` is set.
+void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
+{
+    CgState *s = cg_state(c);
+    const int64_t n = c->nl;
+    c->op.skip = &s->done;
+    c->fix.skip = &s->done;
+    for (int i = 0; i < m; ++i) {
+        if (precision == 64) c->ops->jv_pa_64(c, c->w_cp, c->w_cq, st);
+        else c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
+        { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
+        { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv, n, s, c->w_partial); }
+        { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cp, c->w_cr, c->w_dinv, n, s); }
+    }
+    c->op.skip = nullptr;
+    c->fix.skip = nullptr;
+}
+
+// CG on J x = b (x from 0) with the cached linearisation and preconditioner dinv, on c->own_stream.
+fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int precision, int batch, bool use_graph,
+                 int *iters, int *done_code)
+{
+    cudaStream_t st = c->own_stream;
+    CgState *s = cg_state(c);
+    {
+        LaunchScope ls(c, "cg_init", st);
+        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->nl, s, rtol,
+                                                      max_iter, c->w_partial);
+    }
+    CKLAUNCH();
+    if (batch < 1) batch = 1;
+    const int gi = precision == 64 ? 0 : 1;
+    if (use_graph && (c->cg_exec[gi] == nullptr || c->cg_batch[gi] != batch)) {
+        if (c->cg_exec[gi]) { cudaGraphExecDestroy(c->cg_exec[gi]); c->cg_exec[gi] = nullptr; }
+        const bool prof = c->prof;
+        c->prof = false;
+        const int64_t l0 = c->launches;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        enqueue_cg(c, batch, precision, st);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        c->prof = prof;
+        if (e != cudaSuccess) return fail(c, FE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        c->cg_launches[gi] = c->launches - l0;
+        c->launches = l0;
+        e = cudaGraphInstantiate(&c->cg_exec[gi], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, FE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        c->cg_batch[gi] = batch;
+    }
+    CgState *h = cg_host(c);
+    for (;;) {
+        if (use_graph) {
+            CK(cudaGraphLaunch(c->cg_exec[gi], st));
+            c->launches += c->cg_launches[gi];
+        } else {
+            enqueue_cg(c, batch, precision, st);
+            CKLAUNCH();
+        }
+        CK(cudaMemcpyAsync(h, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (h->done) break;
+    }
+    if (iters) *iters = h->iter;
+    if (done_code) *done_code = h->done;
+    return FE_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// setup
+// ------------------------------------------------------------------------------------------------
+extern "C" fe_status fe_setup(const fe_mesh *mesh, int order, int q1d, const fe_problem *prob, fe_ctx **out)
+{
+    return fe_setup_ex(mesh, order, q1d, prob, nullptr, out);
+}
+
+static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_problem *prob,
+                            const fe_setup_opts *opts)
+{
+    const int dim = mesh->dim, n = mesh->n, k = order;
+    c->dim = dim; c->n = n; c->k = k; c->d1 = k + 1; c->q1 = k + 1;
+    c->NQ = (int)ipow64(c->q1, dim);
+    c->NS = dim == 3 ? 6 : 3;
+    c->NG = c->NS + 2;
+    c->p = prob->p; c->eps = prob->eps; c->f_kind = prob->f_kind; c->f_const = prob->f_const;
+    c->kappa_eps = prob->kappa_eps; c->kappa_q = prob->kappa_q;
+    c->has_rho = prob->rho != nullptr;
+    c->law = (prob->p == 2.0) ? LAW_P2 : (prob->p == 3.0) ? LAW_P3 : (prob->p == 4.0) ? LAW_P4 : LAW_GENERIC;
+    const int64_t m = (int64_t)k * n + 1;
+    c->nl = ipow64(m, dim);
+    c->nfree = ipow64(m - 2 > 0 ? m - 2 : 0, dim);
+    c->ne = ipow64(n, dim);
+    if (c->nl > MAX_DOFS) return fail(c, FE_ERR_UNSUPPORTED, "%lld DOFs exceed the 2^30-1 limit", (long long)c->nl);
+
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    int smem_optin = 0;
+    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+
+    c->ops = find_ops(dim, c->d1);
+    if (!c->ops) return fail(c, FE_ERR_UNSUPPORTED, "no kernels built for dim %d order %d", dim, k);
+
+    // tile size
+    int T = (opts && opts->tile > 0) ? opts->tile : default_tile(dim, k);
+    if (T > n) T = n;
+    const int team = dim == 3 ? c->d1 * c->d1 : c->d1;
+    for (;;) {
+        const int NE = (int)ipow64(T, dim);
+        const int S = (int)ipow64((int64_t)k * T + 1, dim);
+        if (NE * team <= 1024 && c->ops->max_smem(S, T) <= (size_t)smem_optin) break;
+        if (T == 1) return fail(c, FE_ERR_UNSUPPORTED, "order %d does not fit one element per CTA", k);
+        --T;
+    }
+    c->T = T;
+    c->NE = (int)ipow64(T, dim);
+    c->nt = (n + T - 1) / T;
+    c->ntiles = ipow64(c->nt, dim);
+    c->nepad = c->ntiles * c->NE;
+    c->SE = k * T + 1;
+    c->S = (int)ipow64(c->SE, dim);
+    if ((double)c->ntiles * c->S >= 4294967295.0)
+        return fail(c, FE_ERR_UNSUPPORTED, "tile slot index exceeds 32 bits");
+
+    // --- G as explicit index arrays: slot codes per tile, and the transposed halo index ---
+    std::vector<uint32_t> slot((size_t)c->ntiles * c->S);
+    std::vector<uint64_t> halo_pairs;   // (g << 32) | (t*S + s)
+    for (int64_t t = 0; t < c->ntiles; ++t) {
+        int64_t tc[3] = { 0, 0, 0 }, r = t;
+        for (int d = 0; d < dim; ++d) { tc[d] = r % c->nt; r /= c->nt; }
+        for (int s = 0; s < c->S; ++s) {
+            int sc[3] = { s % c->SE, (s / c->SE) % c->SE, dim == 3 ? s / (c->SE * c->SE) : 0 };
+            bool valid = true, ess = false, halo = false;
+            int64_t gl[3] = { 0, 0, 0 };
+            for (int d = 0; d < dim; ++d) {
+                gl[d] = (int64_t)k * T * tc[d] + sc[d];
+                if (gl[d] > (int64_t)k * n) valid = false;
+                if (gl[d] == 0 || gl[d] == (int64_t)k * n) ess = true;
+                if (sc[d] == k * T && tc[d] < c->nt - 1) halo = true;
+            }
+            uint32_t code = SLOT_INVALID;
+            if (valid) {
+                const int64_t g = gl[0] + m * (gl[1] + (dim == 3 ? m * gl[2] : 0));
+                code = (uint32_t)g | (ess ? SLOT_ESS : 0u) | (halo ? SLOT_HALO : 0u);
+                if (halo && !ess) halo_pairs.push_back(((uint64_t)g << 32) | (uint64_t)(t * c->S + s));
+            }
+            slot[(size_t)t * c->S + s] = code;
+        }
+    }
+    std::sort(halo_pairs.begin(), halo_pairs.end());
+    std::vector<uint32_t> fix_g, fix_off, fix_h;
+    fix_h.reserve(halo_pairs.size());
+    for (size_t i = 0; i < halo_pairs.size(); ++i) {
+        const uint32_t g = (uint32_t)(halo_pairs[i] >> 32);
+        if (fix_g.empty() || fix_g.back() != g) { fix_g.push_back(g); fix_off.push_back((uint32_t)fix_h.size()); }
+        fix_h.push_back((uint32_t)(halo_pairs[i] & 0xFFFFFFFFu));
+    }
+    fix_off.push_back((uint32_t)fix_h.size());
+    c->nfix = (int64_t)fix_g.size();
+    c->nfixh = (int64_t)fix_h.size();
+
+    // --- 1D rules and basis tables on [0,1] ---
+    std::vector<double> gx, gw, nodes, val, der;
+    gauss_legendre(c->q1, gx, gw);
+    gll_nodes(k, nodes);
+    std::vector<double> xq(c->q1), xn(c->d1);
+    for (int q = 0; q < c->q1; ++q) { xq[q] = 0.5 * (gx[q] + 1.0); c->gp.xq[q] = xq[q]; c->gp.wq[q] = 0.5 * gw[q]; }
+    for (int a = 0; a < c->d1; ++a) { xn[a] = 0.5 * (nodes[a] + 1.0); c->gp.xn[a] = xn[a]; }
+    lagrange_tables(xn, xq, val, der);     // derivatives w.r.t. the [0,1] coordinate
+    for (int q = 0; q < c->q1; ++q)
+        for (int a = 0; a < c->d1; ++a) {
+            const int i = q * c->d1 + a;
+            const double B = val[i], G = der[i];
+            c->b64.B[i] = B; c->b64.G[i] = G; c->b64.B2[i] = B * B; c->b64.G2[i] = G * G; c->b64.BG[i] = B * G;
+            c->b32.B[i] = (float)B; c->b32.G[i] = (float)G; c->b32.B2[i] = (float)(B * B);
+            c->b32.G2[i] = (float)(G * G); c->b32.BG[i] = (float)(B * G);
+        }
+    c->gp.dim = dim; c->gp.d1 = c->d1; c->gp.q1 = c->q1; c->gp.n = n; c->gp.T = T; c->gp.nt = c->nt;
+    c->gp.nepad = c->nepad; c->gp.f_kind = prob->f_kind; c->gp.f_const = prob->f_const; c->gp.p = prob->p;
+
+    // --- device data ---
+    const int64_t nvert = ipow64(n + 1, dim);
+    CK(dalloc(c, &c->d_slot, slot.size()));
+    CK(cudaMemcpy(c->d_slot, slot.data(), slot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CK(dalloc(c, &c->d_fix_g, fix_g.size()));
+    CK(dalloc(c, &c->d_fix_off, fix_off.size()));
+    CK(dalloc(c, &c->d_fix_h, fix_h.size()));
+    if (!fix_g.empty()) {
+        CK(cudaMemcpy(c->d_fix_g, fix_g.data(), fix_g.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_fix_h, fix_h.data(), fix_h.size() * 4, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(c->d_fix_off, fix_off.data(), fix_off.size() * 4, cudaMemcpyHostToDevice));
+    CK(dalloc(c, &c->d_vert, (size_t)nvert * dim));
+    CK(cudaMemcpy(c->d_vert, mesh->vertices, (size_t)nvert * dim * sizeof(double), cudaMemcpyHostToDevice));
+    CK(dalloc(c, &c->d_geo, (size_t)c->nepad * c->NG * c->NQ));
+    {
+        double *h = nullptr;
+        CK(dalloc(c, &h, (size_t)c->ntiles * c->S));
+        c->d_halo = h;
+    }
+    CK(dalloc(c, &c->d_err, 1));
+    CK(cudaMemset(c->d_err, 0, sizeof(int)));
+
+    {
+        const int64_t total = c->nepad * c->NQ;
+        const int bs = 256;
+        k_geometry<<<(unsigned)((total + bs - 1) / bs), bs>>>(c->gp, c->d_vert, c->d_geo, c->d_err);
+        CKLAUNCH();
+        c->launches++;
+    }
+    if (c->has_rho) {
+        CK(dalloc(c, &c->d_rho, (size_t)c->ne));
+        CK(cudaMemcpy(c->d_rho, prob->rho, (size_t)c->ne * sizeof(double), cudaMemcpyHostToDevice));
+        CK(dalloc(c, &c->d_kr, (size_t)c->nepad));
+        CK(dalloc(c, &c->d_dkr, (size_t)c->nepad));
+        k_design_factors<<<(unsigned)((c->nepad + 255) / 256), 256>>>(c->gp, c->d_rho, c->kappa_eps, c->kappa_q,
+                                                                       c->d_kr, c->d_dkr);
+        CKLAUNCH();
+        c->launches++;
+    }
+    int herr = 0;
+    CK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return fail(c, FE_ERR_MESH, "det J <= 0 at a quadrature point (inverted or degenerate element)");
+
+    // --- kernel parameter blocks ---
+    c->op.n = n; c->op.T = T; c->op.nt = c->nt; c->op.S = c->S; c->op.SE = c->SE; c->op.law = c->law;
+    c->op.ntiles = c->ntiles; c->op.slot = c->d_slot; c->op.geo = c->d_geo;
+    c->op.kr = c->d_kr; c->op.dkr = c->d_dkr; c->op.skip = nullptr;
+    c->op.law_a = 0.5 * (prob->p - 2.0); c->op.eps2 = prob->eps * prob->eps;
+    c->fix.nfix = c->nfix; c->fix.fix_g = c->d_fix_g; c->fix.fix_off = c->d_fix_off; c->fix.fix_h = c->d_fix_h;
+    c->fix.skip = nullptr;
+    CK(c->ops->prepare(c));
+    CK(cudaDeviceSynchronize());
+    return FE_OK;
+}
+
+static thread_local std::string g_setup_error;
+
+extern "C" fe_status fe_setup_ex(const fe_mesh *mesh, int order, int q1d, const fe_problem *prob,
+                                 const fe_setup_opts *opts, fe_ctx **out)
+{
+    if (!out) return FE_ERR_ARG;
+    *out = nullptr;
+    g_setup_error.clear();
+    if (!mesh || !prob || !mesh->vertices || (mesh->dim != 2 && mesh->dim != 3) || mesh->n < 1) {
+        g_setup_error = "invalid mesh or problem";
+        return FE_ERR_ARG;
+    }
+    if (order < 1 || order > MAX_ORDER) { g_setup_error = "order must be 1..6"; return FE_ERR_UNSUPPORTED; }
+    if (q1d != 0 && q1d != order + 1) { g_setup_error = "q1d must be 0 or order+1"; return FE_ERR_UNSUPPORTED; }
+    if (!(prob->p >= 2.0 || (prob->p > 1.0 && prob->eps > 0.0)) || !(prob->eps >= 0.0)) {
+        g_setup_error = "need p >= 2, or p > 1 with eps > 0";
+        return FE_ERR_ARG;
+    }
+    if (prob->f_kind != 0 && prob->f_kind != 1) { g_setup_error = "f_kind must be 0 or 1"; return FE_ERR_ARG; }
+    fe_ctx *c = new (std::nothrow) fe_ctx();
+    if (!c) return FE_ERR_OOM;
+    fe_status s = setup_impl(c, mesh, order, prob, opts);
+    if (s != FE_OK) {
+        g_setup_error = c->err;
+        fe_destroy(c);
+        return s;
+    }
+    *out = c;
+    return FE_OK;
+}
+
+extern "C" void fe_destroy(fe_ctx *c)
+{
+    if (!c) return;
+    void *ptrs[] = { c->d_slot, c->d_fix_g, c->d_fix_off, c->d_fix_h, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
+                     c->d_dkr, c->d_T64, c->d_T32, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
+                     c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_state, c->w_partial };
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    for (auto &g : c->cg_exec)
+        if (g) cudaGraphExecDestroy(g);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    for (auto &r : c->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->prof_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" const char *fe_last_error(const fe_ctx *c)
+{
+    if (!c) return g_setup_error.c_str();
+    return c->err.c_str();
+}
+
+extern "C" const char *fe_status_string(fe_status s)
+{
+    switch (s) {
+    case FE_OK: return "ok";
+    case FE_ERR_ARG: return "invalid argument";
+    case FE_ERR_MESH: return "invalid mesh (det J <= 0)";
+    case FE_ERR_CUDA: return "CUDA error";
+    case FE_ERR_OOM: return "out of memory";
+    case FE_ERR_UNSUPPORTED: return "unsupported";
+    case FE_ERR_NAN: return "NaN or Inf";
+    case FE_ERR_NOT_CONVERGED: return "not converged";
+    case FE_ERR_BREAKDOWN: return "breakdown";
+    case FE_ERR_STATE: return "call out of order";
+    }
+    return "unknown";
+}
+
+extern "C" fe_status fe_num_dofs(const fe_ctx *c, int64_t *n_l, int64_t *n_free)
+{
+    if (!c) return FE_ERR_ARG;
+    if (n_l) *n_l = c->nl;
+    if (n_free) *n_free = c->nfree;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_num_elements(const fe_ctx *c, int64_t *n_e)
+{
+    if (!c || !n_e) return FE_ERR_ARG;
+    *n_e = c->ne;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_memory_bytes(const fe_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return FE_ERR_ARG;
+    *bytes = c->mem_bytes;
+    return FE_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// operators
+// ------------------------------------------------------------------------------------------------
+extern "C" fe_status fe_residual(fe_ctx *c, const double *u, double *r, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!u || !r || u == r) return fail(c, FE_ERR_ARG, "fe_residual: null or aliased vectors");
+    c->ops->residual(c, u, r, nullptr, nullptr, as_stream(stream));
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_linearize(fe_ctx *c, const double *u, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!u) return fail(c, FE_ERR_ARG, "fe_linearize: null u");
+    fe_status s = ensure_tangent(c, true, true);
+    if (s != FE_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    c->ops->residual(c, u, nullptr, c->d_T64, c->d_T32, st);
+    CKLAUNCH();
+    c->ops->diag_64(c, c->d_diag, st);
+    CKLAUNCH();
+    c->lin64 = c->lin32 = c->have_diag = true;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_jacobian_action(fe_ctx *c, const double *u, const void *v, void *y, int precision,
+                                        void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!v || !y || v == y) return fail(c, FE_ERR_ARG, "fe_jacobian_action: null or aliased vectors");
+    cudaStream_t st = as_stream(stream);
+    if (!u) return apply_jv_cached(c, v, y, precision, st);
+    if (precision == 64) c->ops->jv_dual_64(c, u, (const double *)v, (double *)y, st);
+    else if (precision == 32) c->ops->jv_dual_32(c, u, (const float *)v, (float *)y, st);
+    else if (precision == -32) c->ops->jv_dual_32d(c, u, (const double *)v, (double *)y, st);
+    else return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_jacobian_action_host(fe_ctx *c, const void *v_host, void *y_host, int precision,
+                                             void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!v_host || !y_host) return fail(c, FE_ERR_ARG, "fe_jacobian_action_host: null buffers");
+    const size_t es = precision == 32 ? sizeof(float) : sizeof(double);
+    fe_status s = ensure_work(c);
+    if (s != FE_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    // staging in the CG work vectors (each holds N_L doubles)
+    void *dv = c->w_trial, *dy = c->w_d;
+    CK(cudaMemcpyAsync(dv, v_host, es * (size_t)c->nl, cudaMemcpyHostToDevice, st));
+    s = apply_jv_cached(c, dv, dy, precision, st);
+    if (s != FE_OK) return s;
+    CK(cudaMemcpyAsync(y_host, dy, es * (size_t)c->nl, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return FE_OK;
+}
+
+extern "C" fe_status fe_jacobian_diagonal(fe_ctx *c, double *diag, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!diag) return fail(c, FE_ERR_ARG, "fe_jacobian_diagonal: null output");
+    if (!c->have_diag) return fail(c, FE_ERR_STATE, "no linearisation cached (call fe_linearize)");
+    CK(cudaMemcpyAsync(diag, c->d_diag, (size_t)c->nl * sizeof(double), cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return FE_OK;
+}
+
+extern "C" fe_status fe_load_vector(fe_ctx *c, double *F, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!F) return fail(c, FE_ERR_ARG, "fe_load_vector: null output");
+    fe_status s = ensure_work(c);
+    if (s != FE_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    // the flux vanishes at zero gradient, so R(0) = -F (essential entries 0)
+    CK(cudaMemsetAsync(c->w_trial, 0, (size_t)c->nl * sizeof(double), st));
+    c->ops->residual(c, c->w_trial, F, nullptr, nullptr, st);
+    CKLAUNCH();
+    {
+        LaunchScope ls(c, "scale", st);
+        k_scale<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(F, F, -1.0, c->nl);
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_node_coords(fe_ctx *c, double *xyz, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!xyz) return fail(c, FE_ERR_ARG, "fe_node_coords: null output");
+    cudaStream_t st = as_stream(stream);
+    {
+        LaunchScope ls(c, "node_coords", st);
+        k_node_coords<<<(unsigned)((c->nl + 255) / 256), 256, 0, st>>>(c->gp, c->k, c->d_vert, xyz, c->nl);
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_set_design(fe_ctx *c, const double *rho, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!rho) return fail(c, FE_ERR_ARG, "fe_set_design: null rho");
+    if (!c->has_rho) return fail(c, FE_ERR_STATE, "context was set up without a design field");
+    cudaStream_t st = as_stream(stream);
+    CK(cudaMemcpyAsync(c->d_rho, rho, (size_t)c->ne * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    {
+        LaunchScope ls(c, "design_factors", st);
+        k_design_factors<<<(unsigned)((c->nepad + 255) / 256), 256, 0, st>>>(c->gp, c->d_rho, c->kappa_eps,
+                                                                            c->kappa_q, c->d_kr, c->d_dkr);
+    }
+    CKLAUNCH();
+    c->lin64 = c->lin32 = c->have_diag = false;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_adjoint_vjp(fe_ctx *c, const double *u, const double *lambda, double *grad_rho, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!u || !lambda || !grad_rho) return fail(c, FE_ERR_ARG, "fe_adjoint_vjp: null vectors");
+    if (!c->has_rho) return fail(c, FE_ERR_STATE, "fe_adjoint_vjp needs a design field");
+    c->ops->vjp(c, u, lambda, grad_rho, as_stream(stream));
+    CKLAUNCH();
+    return FE_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// solvers
+// ------------------------------------------------------------------------------------------------
+extern "C" fe_status fe_cg_solve(fe_ctx *c, const double *b, double *x, double rtol, int max_iter, int precision,
+                                 int *iters, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!b || !x || b == x) return fail(c, FE_ERR_ARG, "fe_cg_solve: null or aliased vectors");
+    if (precision != 64 && precision != 32) return fail(c, FE_ERR_ARG, "precision must be 64 or 32");
+    if ((precision == 64 && !c->lin64) || (precision == 32 && !c->lin32) || !c->have_diag)
+        return fail(c, FE_ERR_STATE, "no linearisation cached (call fe_linearize)");
+    fe_status s = ensure_work(c);
+    if (s != FE_OK) return s;
+    CK(cudaStreamSynchronize(as_stream(stream)));
+    cudaStream_t st = c->own_stream;
+    {
+        LaunchScope ls(c, "reciprocal", st);
+        k_reciprocal<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_dinv, c->d_diag, c->nl);
+    }
+    CKLAUNCH();
+    int it = 0, done = 0;
+    s = run_cg(c, b, rtol, max_iter, precision == 64 ? 64 : -32, 16, true, &it, &done);
+    if (s != FE_OK) return s;
+    CK(cudaMemcpyAsync(x, c->w_cx, (size_t)c->nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (iters) *iters = it;
+    if (done == CG_BREAKDOWN) return fail(c, FE_ERR_BREAKDOWN, "CG breakdown (p^T J p <= 0)");
+    if (done == CG_NAN) return fail(c, FE_ERR_NAN, "CG produced NaN/Inf");
+    if (done == CG_MAXIT) return fail(c, FE_ERR_NOT_CONVERGED, "CG reached %d iterations", max_iter);
+    return FE_OK;
+}
+
+extern "C" fe_status fe_newton_default_opts(fe_newton_opts *o)
+{
+    if (!o) return FE_ERR_ARG;
+    o->rtol = 1e-8;
+    o->max_newton = 50;
+    o->max_cg = 20000;
+    o->cg_rtol = 1e-4;
+    o->inner_precision = 64;
+    o->line_search = 1;
+    o->armijo = 1e-4;
+    o->max_halvings = 20;
+    o->cg_batch = 16;
+    o->use_graph = 1;
+    return FE_OK;
+}
+
+extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *opts_in, fe_newton_report *rep,
+                                  void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!u) return fail(c, FE_ERR_ARG, "newton_solve: null u");
+    fe_newton_opts o;
+    if (opts_in) o = *opts_in; else fe_newton_default_opts(&o);
+    if (o.inner_precision != 64 && o.inner_precision != 32)
+        return fail(c, FE_ERR_ARG, "inner_precision must be 64 or 32");
+    fe_newton_report R;
+    std::memset(&R, 0, sizeof R);
+    const bool mixed = o.inner_precision == 32;
+    fe_status s = ensure_work(c);
+    if (s == FE_OK) s = ensure_tangent(c, !mixed, mixed);
+    if (s != FE_OK) return s;
+    CK(cudaStreamSynchronize(as_stream(stream)));
+    cudaStream_t st = c->own_stream;
+    const int64_t l0 = c->launches;
+    const auto t0 = std::chrono::steady_clock::now();
+    double cg_ms = 0.0;
+    double *T64 = mixed ? nullptr : c->d_T64;
+    float *T32 = mixed ? c->d_T32 : nullptr;
+    const int jprec = mixed ? -32 : 64;
+
+    // R and J_D at u (fused)
+    c->ops->residual(c, u, c->w_r, T64, T32, st);
+    CKLAUNCH();
+    double rr = 0.0;
+    s = dot_sync(c, c->w_r, c->w_r, &rr, st);
+    if (s != FE_OK) return s;
+    double rnorm = std::sqrt(rr);
+    R.r0 = rnorm;
+    fe_status result = FE_OK;
+    if (!std::isfinite(rnorm)) result = fail(c, FE_ERR_NAN, "initial residual is not finite");
+    int it = 0;
+    while (result == FE_OK && rnorm > o.rtol * R.r0 && R.r0 > 0.0) {
+        if (it >= o.max_newton) { result = fail(c, FE_ERR_NOT_CONVERGED, "Newton reached %d steps", it); break; }
+        // Jacobi preconditioner of the current linearisation
+        if (mixed) c->ops->diag_32(c, c->d_diag, st); else c->ops->diag_64(c, c->d_diag, st);
+        CKLAUNCH();
+        {
+            LaunchScope ls(c, "reciprocal", st);
+            k_reciprocal<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_dinv, c->d_diag, c->nl);
+        }
+        // right-hand side -R
+        {
+            LaunchScope ls(c, "scale", st);
+            k_scale<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_d, c->w_r, -1.0, c->nl);
+        }
+        CKLAUNCH();
+        const auto c0 = std::chrono::steady_clock::now();
+        int cg_it = 0, done = 0;
+        s = run_cg(c, c->w_d, o.cg_rtol, o.max_cg, jprec, o.cg_batch, o.use_graph != 0, &cg_it, &done);
+        if (s != FE_OK) return s;
+        cg_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c0).count();
+        R.cg_iters_total += cg_it;
+        if (it < FE_NEWTON_HIST) R.cg_hist[it] = cg_it;
+        if (done == CG_BREAKDOWN || done == CG_NAN) {
+            result = fail(c, done == CG_NAN ? FE_ERR_NAN : FE_ERR_BREAKDOWN, "inner CG failed (%d)", done);
+            break;
+        }
+        // backtracking line search on ||R||: trial = u + alpha d (d = CG solution in w_cx)
+        double alpha = 1.0, tn = 0.0;
+        bool accepted = false;
+        for (int h = 0; h <= o.max_halvings; ++h) {
+            {
+                LaunchScope ls(c, "waxpy", st);
+                k_waxpy<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_trial, u, alpha, c->w_cx, c->nl);
+            }
+            c->ops->residual(c, c->w_trial, c->w_d, T64, T32, st);
+            CKLAUNCH();
+            s = dot_sync(c, c->w_d, c->w_d, &tn, st);
+            if (s != FE_OK) return s;
+            tn = std::sqrt(tn);
+            if (std::isfinite(tn) && (!o.line_search || tn <= (1.0 - o.armijo * alpha) * rnorm)) { accepted = true; break; }
+            if (!o.line_search) break;
+            alpha *= 0.5;
+            R.line_search_halvings++;
+        }
+        if (!accepted) { result = fail(c, FE_ERR_BREAKDOWN, "line search failed at Newton step %d", it); break; }
+        CK(cudaMemcpyAsync(u, c->w_trial, (size_t)c->nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        std::swap(c->w_r, c->w_d);
+        rnorm = tn;
+        if (it < FE_NEWTON_HIST) R.r_hist[it] = rnorm;
+        ++it;
+    }
+    CK(cudaStreamSynchronize(st));
+    c->lin64 = !mixed; c->lin32 = mixed; c->have_diag = false;
+    R.newton_iters = it;
+    R.r_final = rnorm;
+    R.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    R.t_cg_ms = cg_ms;
+    R.kernel_launches = c->launches - l0;
+    R.status = result;
+    if (rep) *rep = R;
+    return result;
+}
+
+// ------------------------------------------------------------------------------------------------
+// profiling
+// ------------------------------------------------------------------------------------------------
+extern "C" fe_status fe_prof_enable(fe_ctx *c, int enable)
+{
+    if (!c) return FE_ERR_ARG;
+    c->prof = enable != 0;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_prof_reset(fe_ctx *c)
+{
+    if (!c) return FE_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    for (auto &r : c->prof_recs) { c->prof_pool.push_back(r.a); c->prof_pool.push_back(r.b); }
+    c->prof_recs.clear();
+    std::fill(c->prof_count.begin(), c->prof_count.end(), 0);
+    std::fill(c->prof_ms.begin(), c->prof_ms.end(), 0.0);
+    c->launches = 0;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_prof_read(fe_ctx *c, int i, const char **name, int64_t *launches, double *ms, int *count)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!c->prof_recs.empty()) {
+        CK(cudaDeviceSynchronize());
+        for (auto &r : c->prof_recs) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, r.a, r.b));
+            c->prof_ms[r.name] += t;
+            c->prof_count[r.name] += 1;
+            c->prof_pool.push_back(r.a);
+            c->prof_pool.push_back(r.b);
+        }
+        c->prof_recs.clear();
+    }
+    if (count) *count = (int)c->prof_names.size();
+    if (i >= 0 && i < (int)c->prof_names.size()) {
+        if (name) *name = c->prof_names[i].c_str();
+        if (launches) *launches = c->prof_count[i];
+        if (ms) *ms = c->prof_ms[i];
+    }
+    return FE_OK;
+}
+
+extern "C" fe_status fe_launch_count(const fe_ctx *c, int64_t *launches)
+{
+    if (!c || !launches) return FE_ERR_ARG;
+    *launches = c->launches;
+    return FE_OK;
+}

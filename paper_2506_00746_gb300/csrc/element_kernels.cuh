@@ -1,0 +1,1047 @@
+// element_kernels.cuh -- the matrix-free FEOD operator kernels for sm_103a.
+//
+// One CTA owns one tile of T^dim elements of the structured lattice.  Per tile:
+//   G   : the tile's DOF block (its "slots", (kT+1)^dim values) is gathered from the L-vector into
+//         shared memory once through the explicit slot index (P applied on the way: essential
+//         entries of a Jacobian input are zeroed);
+//   B   : each element is handled by a team of (k+1)^(dim-1) threads, each owning one line of
+//         (k+1) values in registers; the tensor-product contractions (interpolation B^ and
+//         derivative G^ per direction, sum factorisation) run along the owned line, with
+//         shared-memory transposes between directions;
+//   D   : the pointwise operator at each quadrature point -- the p-Laplacian flux written once
+//         over a scalar type and evaluated with forward-mode dual numbers for its derivative
+//         (Eq. 2: J_D = dD/du_q), or the stored tangent (partial assembly);
+//   B^T : the transposed contractions;
+//   G^T : element results are staged in shared memory and every slot sums the (at most 2^dim)
+//         element contributions in a fixed order; slots owned by the tile are written to the
+//         output, slots owned by a neighbouring tile go to a halo buffer that a second small
+//         kernel adds in a fixed order.  No floating-point atomics: results are bitwise
+//         reproducible.
+// Everything is a template over (dim, k+1, compute type, I/O type).
+#pragma once
+
+#include "internal.h"
+
+namespace feod {
+
+// --------------------------------------------------------------------------------------------
+// Forward-mode dual numbers (value + N directional derivatives)
+// --------------------------------------------------------------------------------------------
+template <typename T, int N>
+struct Dual {
+    T v;
+    T d[N];
+};
+
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator+(const Dual<T, N> &a, const Dual<T, N> &b)
+{
+    Dual<T, N> r; r.v = a.v + b.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+    return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator+(const Dual<T, N> &a, T b)
+{
+    Dual<T, N> r = a; r.v = a.v + b; return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator*(const Dual<T, N> &a, const Dual<T, N> &b)
+{
+    Dual<T, N> r; r.v = a.v * b.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator*(T a, const Dual<T, N> &b)
+{
+    Dual<T, N> r; r.v = a * b.v;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = a * b.d[i];
+    return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> operator*(const Dual<T, N> &a, T b) { return b * a; }
+
+__device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float f_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double f_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float f_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double f_pow(double x, double a) { return pow(x, a); }
+__device__ __forceinline__ float f_pow(float x, float a) { return powf(x, a); }
+
+// kappa(base) = base^a, a = (p-2)/2, with the limit values at base == 0 (kappa = 1 for p = 2,
+// else 0 for a > 0; the derivative term is taken as 0 there, which is the limit of d(kappa g)).
+template <typename T>
+__device__ __forceinline__ T kappa_of(T base, int law, T a)
+{
+    switch (law) {
+    case LAW_P2: return T(1);
+    case LAW_P3: return f_sqrt(base);
+    case LAW_P4: return base;
+    default: return base == T(0) ? (a == T(0) ? T(1) : T(0)) : f_pow(base, a);
+    }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ Dual<T, N> kappa_of(const Dual<T, N> &base, int law, T a)
+{
+    T kv, kp;   // value and d kappa / d base
+    switch (law) {
+    case LAW_P2: kv = T(1); kp = T(0); break;
+    case LAW_P3:
+        if (base.v == T(0)) { kv = T(0); kp = T(0); }
+        else { T r = f_rsqrt(base.v); kv = base.v * r; kp = T(0.5) * r; }
+        break;
+    case LAW_P4: kv = base.v; kp = T(1); break;
+    default:
+        if (base.v == T(0)) { kv = (a == T(0)) ? T(1) : T(0); kp = T(0); }
+        else { kv = f_pow(base.v, a); kp = a * kv / base.v; }
+    }
+    Dual<T, N> r; r.v = kv;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = kp * base.d[i];
+    return r;
+}
+
+// The pointwise operator D of the p-Laplacian in reference coordinates.  With M = w detJ J^-1 J^-T
+// (stored symmetric) and iw = 1/(w detJ):  sigma = |grad u|^2 = g^T M g * iw,
+// q = kr * kappa(eps^2 + sigma) * M g, where g is the reference gradient.  Written once over the
+// scalar type S (real or dual); kr (kappa_rho of the element) may be real or dual.
+// 3D symmetric order: xx, yy, zz, xy, xz, yz.
+template <typename S, typename T, typename K>
+__device__ __forceinline__ void flux3(const S (&g)[3], const T (&M)[6], T iw, K kr, int law, T a,
+                                      T eps2, S (&q)[3])
+{
+    S m0 = M[0] * g[0] + M[3] * g[1] + M[4] * g[2];
+    S m1 = M[3] * g[0] + M[1] * g[1] + M[5] * g[2];
+    S m2 = M[4] * g[0] + M[5] * g[1] + M[2] * g[2];
+    S sig = (g[0] * m0 + g[1] * m1 + g[2] * m2) * iw;
+    S kap = kr * kappa_of(sig + eps2, law, a);
+    q[0] = kap * m0; q[1] = kap * m1; q[2] = kap * m2;
+}
+
+// 2D symmetric order: xx, yy, xy.
+template <typename S, typename T, typename K>
+__device__ __forceinline__ void flux2(const S (&g)[2], const T (&M)[3], T iw, K kr, int law, T a,
+                                      T eps2, S (&q)[2])
+{
+    S m0 = M[0] * g[0] + M[2] * g[1];
+    S m1 = M[2] * g[0] + M[1] * g[1];
+    S sig = (g[0] * m0 + g[1] * m1) * iw;
+    S kap = kr * kappa_of(sig + eps2, law, a);
+    q[0] = kap * m0; q[1] = kap * m1;
+}
+
+// --------------------------------------------------------------------------------------------
+// Shapes and tile bookkeeping
+// --------------------------------------------------------------------------------------------
+template <int DIM, int D1>
+struct Shape {
+    static constexpr int TEAM = DIM == 3 ? D1 * D1 : D1;          // threads per element
+    static constexpr int NQ = DIM == 3 ? D1 * D1 * D1 : D1 * D1;  // points (= nodes) per element
+    static constexpr int NS = DIM == 3 ? 6 : 3;                   // symmetric tangent entries
+    static constexpr int NG = NS + 2;                             // M, 1/(w detJ), w detJ f
+    static constexpr int K = D1 - 1;                              // order
+};
+
+// quadrature point index of the i-th point held by a thread (3D: x-line of (qy,qz) = lane;
+// 2D: y-line of qx = lane); q = qx + D1 (qy + D1 qz)
+template <int DIM, int D1>
+__device__ __forceinline__ int qidx(int lane, int i)
+{
+    return DIM == 3 ? i + D1 * lane : lane + D1 * i;
+}
+
+struct TileInfo {
+    int T1[3];    // tile coordinates
+    int nv[3];    // valid elements of the tile per direction (ragged last tile)
+};
+
+template <int DIM>
+__device__ __forceinline__ TileInfo tile_info(const OpParams &P, int64_t t)
+{
+    TileInfo ti;
+    int64_t r = t;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d < DIM) {
+            ti.T1[d] = (int)(r % P.nt); r /= P.nt;
+            int rem = P.n - ti.T1[d] * P.T;
+            ti.nv[d] = rem < P.T ? rem : P.T;
+        } else {
+            ti.T1[d] = 0; ti.nv[d] = 1;
+        }
+    }
+    return ti;
+}
+
+template <int DIM>
+__device__ __forceinline__ void elem_coords(int el, int T, int (&c)[3])
+{
+    c[0] = el % T;
+    c[1] = (el / T) % T;
+    c[2] = DIM == 3 ? el / (T * T) : 0;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool elem_valid(const TileInfo &ti, const int (&c)[3])
+{
+    return c[0] < ti.nv[0] && c[1] < ti.nv[1] && (DIM == 2 || c[2] < ti.nv[2]);
+}
+
+// Public (lexicographic) element number of a tile-local element.
+template <int DIM>
+__device__ __forceinline__ int64_t elem_public(const OpParams &P, const TileInfo &ti, const int (&c)[3])
+{
+    int64_t ex = (int64_t)ti.T1[0] * P.T + c[0], ey = (int64_t)ti.T1[1] * P.T + c[1];
+    int64_t ez = (int64_t)ti.T1[2] * P.T + c[2];
+    return ex + P.n * (ey + (DIM == 3 ? P.n * ez : 0));
+}
+
+// G (and P for a Jacobian input): gather the tile's DOF block into shared memory.
+template <typename TC, typename TIN, bool MASK_ESSENTIAL>
+__device__ __forceinline__ void load_slots(const OpParams &P, int64_t t, const TIN *__restrict__ v, TC *Vs)
+{
+    const uint32_t *sl = P.slot + t * P.S;
+    for (int s = threadIdx.x; s < P.S; s += blockDim.x) {
+        uint32_t c = sl[s];
+        TC val = TC(0);
+        if (c != SLOT_INVALID && !(MASK_ESSENTIAL && (c & SLOT_ESS))) val = (TC)v[c & SLOT_GMASK];
+        Vs[s] = val;
+    }
+}
+
+// The team's input line: 3D thread (ti,tj) takes the z-line at local (x,y) = (ti,tj);
+// 2D thread ti takes the x-line at local y = ti.
+template <int DIM, int D1, typename TC>
+__device__ __forceinline__ void gather_line(const OpParams &P, const TC *Vs, const int (&ec)[3], int lane,
+                                            TC (&u)[D1])
+{
+    constexpr int K = D1 - 1;
+    const int SE = P.SE;
+    if (DIM == 3) {
+        const int ti = lane % D1, tj = lane / D1;
+        const int base = (K * ec[0] + ti) + SE * ((K * ec[1] + tj) + SE * (K * ec[2]));
+#pragma unroll
+        for (int c = 0; c < D1; ++c) u[c] = Vs[base + SE * SE * c];
+    } else {
+        const int base = K * ec[0] + SE * (K * ec[1] + lane);
+#pragma unroll
+        for (int a = 0; a < D1; ++a) u[a] = Vs[base + a];
+    }
+}
+
+// Stage the element's output line in Ye (local node order a + D1 (b + D1 c)).
+template <int DIM, int D1, typename TC>
+__device__ __forceinline__ void store_line(TC *Ye, int lane, const TC (&y)[D1])
+{
+    if (DIM == 3) {
+        const int ti = lane % D1, tj = lane / D1;
+#pragma unroll
+        for (int c = 0; c < D1; ++c) Ye[ti + D1 * (tj + D1 * c)] = y[c];
+    } else {
+#pragma unroll
+        for (int a = 0; a < D1; ++a) Ye[a + D1 * lane] = y[a];
+    }
+}
+
+enum OutMode { OUT_JV = 0, OUT_RES = 1, OUT_DIAG = 2 };
+
+// G^T inside the tile, then the write: every slot sums the contributions of the (at most 2 per
+// direction) elements that contain it, in ascending (z, y, x) element order.  Owned slots are
+// written (essential rows: J v -> v_i, residual -> 0, diagonal -> 1); halo slots go to
+// halo[t*S + s] for the fix-up kernel.
+template <int DIM, int D1, typename TC, typename TIO, int OUT>
+__device__ __forceinline__ void scatter_tile(const OpParams &P, int64_t t, const TileInfo &ti, const TC *Ye,
+                                             TIO *__restrict__ y, const TIO *__restrict__ vorig,
+                                             TC *__restrict__ halo)
+{
+    constexpr int K = D1 - 1;
+    constexpr int NQ = Shape<DIM, D1>::NQ;
+    const int SE = P.SE, T = P.T;
+    const uint32_t *sl = P.slot + t * P.S;
+    for (int s = threadIdx.x; s < P.S; s += blockDim.x) {
+        const uint32_t code = sl[s];
+        if (code == SLOT_INVALID) continue;
+        int sc[3] = { s % SE, (s / SE) % SE, DIM == 3 ? s / (SE * SE) : 0 };
+        // candidate (element coordinate, local node) pairs per direction, ascending
+        int ce[3][2], cl[3][2], cn[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cn[d] = 0;
+            if (d >= DIM) { ce[d][0] = 0; cl[d][0] = 0; cn[d] = 1; continue; }
+            const int t1 = sc[d] / K;
+            if (t1 >= 1 && sc[d] - K * t1 == 0 && t1 - 1 < ti.nv[d]) { ce[d][cn[d]] = t1 - 1; cl[d][cn[d]] = K; cn[d]++; }
+            if (t1 < T && t1 < ti.nv[d]) { ce[d][cn[d]] = t1; cl[d][cn[d]] = sc[d] - K * t1; cn[d]++; }
+        }
+        TC acc = TC(0);
+        for (int iz = 0; iz < cn[2]; ++iz)
+            for (int iy = 0; iy < cn[1]; ++iy)
+                for (int ix = 0; ix < cn[0]; ++ix) {
+                    const int el = ce[0][ix] + T * (ce[1][iy] + T * ce[2][iz]);
+                    const int lo = cl[0][ix] + D1 * (cl[1][iy] + D1 * cl[2][iz]);
+                    acc += Ye[el * NQ + lo];
+                }
+        const uint32_t g = code & SLOT_GMASK;
+        if (code & SLOT_HALO) {
+            if (!(code & SLOT_ESS)) halo[t * P.S + s] = acc;
+        } else if (code & SLOT_ESS) {
+            if (OUT == OUT_JV) y[g] = vorig[g];
+            else if (OUT == OUT_RES) y[g] = TIO(0);
+            else y[g] = TIO(1);
+        } else {
+            y[g] = (TIO)acc;
+        }
+    }
+}
+
+// Fix-up: y[g] = y[g] + sum of the halo partial sums of g, in ascending tile order, accumulated
+// in the compute type TC.
+template <typename TC, typename TIO>
+__global__ void k_fixup(const FixParams F, const TC *__restrict__ halo, TIO *__restrict__ y)
+{
+    if (F.skip && *F.skip) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= F.nfix) return;
+    const uint32_t g = F.fix_g[r];
+    TC acc = (TC)y[g];
+    const uint32_t j1 = F.fix_off[r + 1];
+    for (uint32_t j = F.fix_off[r]; j < j1; ++j) acc += halo[F.fix_h[j]];
+    y[g] = (TIO)acc;
+}
+
+// --------------------------------------------------------------------------------------------
+// Sum-factorised B and B^T
+// --------------------------------------------------------------------------------------------
+// Per element, two scratch blocks b0, b1 of 3*NQ values each, layout [array][z][y][x].
+
+// 3D forward: reference gradient at the thread's x-line of quadrature points.
+//   gx = G_x B_y B_z u,  gy = B_x G_y B_z u,  gz = B_x B_y G_z u.
+template <int D1, typename TC>
+__device__ __forceinline__ void fwd3(const TC (&u)[D1], TC *b0, TC *b1, const BasisT<TC> &Bs, int lane,
+                                     TC (&g)[3][D1])
+{
+    constexpr int NQ = D1 * D1 * D1;
+    const int ti = lane % D1, tj = lane / D1;
+    // z contraction: thread (x, y) = (ti, tj)
+#pragma unroll
+    for (int qz = 0; qz < D1; ++qz) {
+        TC a0 = TC(0), a1 = TC(0);
+#pragma unroll
+        for (int c = 0; c < D1; ++c) { a0 += Bs.B[qz * D1 + c] * u[c]; a1 += Bs.G[qz * D1 + c] * u[c]; }
+        b0[(qz * D1 + tj) * D1 + ti] = a0;
+        b0[NQ + (qz * D1 + tj) * D1 + ti] = a1;
+    }
+    __syncthreads();
+    // y contraction: thread (x, qz) = (ti, tj)
+    {
+        TC a0[D1], a1[D1];
+#pragma unroll
+        for (int b = 0; b < D1; ++b) {
+            a0[b] = b0[(tj * D1 + b) * D1 + ti];
+            a1[b] = b0[NQ + (tj * D1 + b) * D1 + ti];
+        }
+#pragma unroll
+        for (int qy = 0; qy < D1; ++qy) {
+            TC c00 = TC(0), c01 = TC(0), c10 = TC(0);
+#pragma unroll
+            for (int b = 0; b < D1; ++b) {
+                c00 += Bs.B[qy * D1 + b] * a0[b];
+                c01 += Bs.G[qy * D1 + b] * a0[b];
+                c10 += Bs.B[qy * D1 + b] * a1[b];
+            }
+            b1[(tj * D1 + qy) * D1 + ti] = c00;
+            b1[NQ + (tj * D1 + qy) * D1 + ti] = c01;
+            b1[2 * NQ + (tj * D1 + qy) * D1 + ti] = c10;
+        }
+    }
+    __syncthreads();
+    // x contraction: thread (qy, qz) = (ti, tj)
+    {
+        TC c00[D1], c01[D1], c10[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) {
+            c00[a] = b1[(tj * D1 + ti) * D1 + a];
+            c01[a] = b1[NQ + (tj * D1 + ti) * D1 + a];
+            c10[a] = b1[2 * NQ + (tj * D1 + ti) * D1 + a];
+        }
+#pragma unroll
+        for (int qx = 0; qx < D1; ++qx) {
+            TC gx = TC(0), gy = TC(0), gz = TC(0);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                gx += Bs.G[qx * D1 + a] * c00[a];
+                gy += Bs.B[qx * D1 + a] * c01[a];
+                gz += Bs.B[qx * D1 + a] * c10[a];
+            }
+            g[0][qx] = gx; g[1][qx] = gy; g[2][qx] = gz;
+        }
+    }
+}
+
+// 3D transpose: y = B_z^T B_y^T (G_x^T fx + B_x^T s) + B_z^T G_y^T B_x^T fy + G_z^T B_y^T B_x^T fz,
+// returned on the thread's z-line (local x, y) = (ti, tj).
+template <int D1, typename TC, bool HAS_S>
+__device__ __forceinline__ void bwd3(const TC (&f)[3][D1], const TC (&s)[D1], TC *b0, TC *b1,
+                                     const BasisT<TC> &Bs, int lane, TC (&y)[D1])
+{
+    constexpr int NQ = D1 * D1 * D1;
+    const int ti = lane % D1, tj = lane / D1;
+    // x: thread (qy, qz) = (ti, tj) -> [qz][qy][a]
+#pragma unroll
+    for (int a = 0; a < D1; ++a) {
+        TC d00 = TC(0), d01 = TC(0), d10 = TC(0);
+#pragma unroll
+        for (int qx = 0; qx < D1; ++qx) {
+            d00 += Bs.G[qx * D1 + a] * f[0][qx];
+            if (HAS_S) d00 += Bs.B[qx * D1 + a] * s[qx];
+            d01 += Bs.B[qx * D1 + a] * f[1][qx];
+            d10 += Bs.B[qx * D1 + a] * f[2][qx];
+        }
+        b0[(tj * D1 + ti) * D1 + a] = d00;
+        b0[NQ + (tj * D1 + ti) * D1 + a] = d01;
+        b0[2 * NQ + (tj * D1 + ti) * D1 + a] = d10;
+    }
+    __syncthreads();
+    // y: thread (a, qz) = (ti, tj) -> [qz][b][a]
+    {
+        TC e00[D1], e01[D1], e10[D1];
+#pragma unroll
+        for (int qy = 0; qy < D1; ++qy) {
+            e00[qy] = b0[(tj * D1 + qy) * D1 + ti];
+            e01[qy] = b0[NQ + (tj * D1 + qy) * D1 + ti];
+            e10[qy] = b0[2 * NQ + (tj * D1 + qy) * D1 + ti];
+        }
+#pragma unroll
+        for (int b = 0; b < D1; ++b) {
+            TC E0 = TC(0), E1 = TC(0);
+#pragma unroll
+            for (int qy = 0; qy < D1; ++qy) {
+                E0 += Bs.B[qy * D1 + b] * e00[qy] + Bs.G[qy * D1 + b] * e01[qy];
+                E1 += Bs.B[qy * D1 + b] * e10[qy];
+            }
+            b1[(tj * D1 + b) * D1 + ti] = E0;
+            b1[NQ + (tj * D1 + b) * D1 + ti] = E1;
+        }
+    }
+    __syncthreads();
+    // z: thread (a, b) = (ti, tj)
+    {
+        TC z0[D1], z1[D1];
+#pragma unroll
+        for (int qz = 0; qz < D1; ++qz) {
+            z0[qz] = b1[(qz * D1 + tj) * D1 + ti];
+            z1[qz] = b1[NQ + (qz * D1 + tj) * D1 + ti];
+        }
+#pragma unroll
+        for (int c = 0; c < D1; ++c) {
+            TC acc = TC(0);
+#pragma unroll
+            for (int qz = 0; qz < D1; ++qz) acc += Bs.B[qz * D1 + c] * z0[qz] + Bs.G[qz * D1 + c] * z1[qz];
+            y[c] = acc;
+        }
+    }
+}
+
+// 2D forward: gx = G_x B_y u, gy = B_x G_y u at the y-line of qx = lane.  Writes b0 only.
+template <int D1, typename TC>
+__device__ __forceinline__ void fwd2(const TC (&u)[D1], TC *b0, const BasisT<TC> &Bs, int lane,
+                                     TC (&g)[2][D1])
+{
+    constexpr int NQ = D1 * D1;
+#pragma unroll
+    for (int qx = 0; qx < D1; ++qx) {
+        TC a0 = TC(0), a1 = TC(0);
+#pragma unroll
+        for (int a = 0; a < D1; ++a) { a0 += Bs.B[qx * D1 + a] * u[a]; a1 += Bs.G[qx * D1 + a] * u[a]; }
+        b0[lane * D1 + qx] = a0;
+        b0[NQ + lane * D1 + qx] = a1;
+    }
+    __syncthreads();
+    TC a0[D1], a1[D1];
+#pragma unroll
+    for (int b = 0; b < D1; ++b) { a0[b] = b0[b * D1 + lane]; a1[b] = b0[NQ + b * D1 + lane]; }
+#pragma unroll
+    for (int qy = 0; qy < D1; ++qy) {
+        TC gx = TC(0), gy = TC(0);
+#pragma unroll
+        for (int b = 0; b < D1; ++b) { gx += Bs.B[qy * D1 + b] * a1[b]; gy += Bs.G[qy * D1 + b] * a0[b]; }
+        g[0][qy] = gx; g[1][qy] = gy;
+    }
+}
+
+// 2D transpose: y = G_x^T B_y^T fx + B_x^T (G_y^T fy + B_y^T s) on the x-line of local y = lane.
+// Writes b1 only.
+template <int D1, typename TC, bool HAS_S>
+__device__ __forceinline__ void bwd2(const TC (&f)[2][D1], const TC (&s)[D1], TC *b1, const BasisT<TC> &Bs,
+                                     int lane, TC (&y)[D1])
+{
+    constexpr int NQ = D1 * D1;
+#pragma unroll
+    for (int b = 0; b < D1; ++b) {
+        TC p1 = TC(0), p0 = TC(0);
+#pragma unroll
+        for (int qy = 0; qy < D1; ++qy) {
+            p1 += Bs.B[qy * D1 + b] * f[0][qy];
+            p0 += Bs.G[qy * D1 + b] * f[1][qy];
+            if (HAS_S) p0 += Bs.B[qy * D1 + b] * s[qy];
+        }
+        b1[b * D1 + lane] = p1;
+        b1[NQ + b * D1 + lane] = p0;
+    }
+    __syncthreads();
+    TC p1[D1], p0[D1];
+#pragma unroll
+    for (int qx = 0; qx < D1; ++qx) { p1[qx] = b1[lane * D1 + qx]; p0[qx] = b1[NQ + lane * D1 + qx]; }
+#pragma unroll
+    for (int a = 0; a < D1; ++a) {
+        TC acc = TC(0);
+#pragma unroll
+        for (int qx = 0; qx < D1; ++qx) acc += Bs.G[qx * D1 + a] * p1[qx] + Bs.B[qx * D1 + a] * p0[qx];
+        y[a] = acc;
+    }
+}
+
+template <int DIM, int D1, typename TC>
+__device__ __forceinline__ void fwd(const TC (&u)[D1], TC *b0, TC *b1, const BasisT<TC> &Bs, int lane,
+                                    TC (&g)[DIM][D1])
+{
+    if constexpr (DIM == 3) fwd3<D1, TC>(u, b0, b1, Bs, lane, g);
+    else fwd2<D1, TC>(u, b0, Bs, lane, g);
+}
+
+template <int DIM, int D1, typename TC, bool HAS_S>
+__device__ __forceinline__ void bwd(const TC (&f)[DIM][D1], const TC (&s)[D1], TC *b0, TC *b1,
+                                    const BasisT<TC> &Bs, int lane, TC (&y)[D1])
+{
+    if constexpr (DIM == 3) bwd3<D1, TC, HAS_S>(f, s, b0, b1, Bs, lane, y);
+    else bwd2<D1, TC, HAS_S>(f, s, b1, Bs, lane, y);
+}
+
+// Shared memory layout of every element kernel: [Vs: n_inputs * S_pad][bufs: NE * 6 * NQ][Ye: NE * NQ]
+__host__ __device__ inline int pad4(int s) { return (s + 3) & ~3; }
+
+template <int DIM, int D1>
+__host__ __device__ inline size_t smem_bytes(int S, int T, size_t tc, int n_inputs)
+{
+    const int NE = DIM == 3 ? T * T * T : T * T;
+    return tc * ((size_t)n_inputs * pad4(S) + (size_t)NE * 7 * Shape<DIM, D1>::NQ);
+}
+
+// --------------------------------------------------------------------------------------------
+// Kernels
+// --------------------------------------------------------------------------------------------
+
+// Partially assembled Jacobian action: y = P^T G^T B^T (T_q . B G P v).
+template <int DIM, int D1, typename TC, typename TIO>
+__global__ void k_jv_pa(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
+                        const TC *__restrict__ Tq, const TIO *__restrict__ v, TIO *__restrict__ y,
+                        TC *__restrict__ halo)
+{
+    using SH = Shape<DIM, D1>;
+    if (P.skip && *P.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = P.T;
+    const int NE = DIM == 3 ? T * T * T : T * T;
+    TC *Vs = reinterpret_cast<TC *>(smem);
+    TC *bufs = Vs + pad4(P.S);
+    TC *Ye = bufs + NE * 6 * SH::NQ;
+    const int64_t t = blockIdx.x;
+    const TileInfo tinf = tile_info<DIM>(P, t);
+    load_slots<TC, TIO, true>(P, t, v, Vs);
+    __syncthreads();
+    const int el = threadIdx.x / SH::TEAM, lane = threadIdx.x % SH::TEAM;
+    int ec[3];
+    elem_coords<DIM>(el, T, ec);
+    TC *b0 = bufs + el * 6 * SH::NQ, *b1 = b0 + 3 * SH::NQ;
+    TC u[D1];
+    gather_line<DIM, D1, TC>(P, Vs, ec, lane, u);
+    TC g[DIM][D1];
+    fwd<DIM, D1, TC>(u, b0, b1, Bs, lane, g);
+    const TC *Te = Tq + (t * NE + el) * (int64_t)(SH::NS * SH::NQ);
+    TC f[DIM][D1], s[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        const int q = qidx<DIM, D1>(lane, i);
+        if constexpr (DIM == 3) {
+            const TC txx = Te[q], tyy = Te[SH::NQ + q], tzz = Te[2 * SH::NQ + q];
+            const TC txy = Te[3 * SH::NQ + q], txz = Te[4 * SH::NQ + q], tyz = Te[5 * SH::NQ + q];
+            f[0][i] = txx * g[0][i] + txy * g[1][i] + txz * g[2][i];
+            f[1][i] = txy * g[0][i] + tyy * g[1][i] + tyz * g[2][i];
+            f[2][i] = txz * g[0][i] + tyz * g[1][i] + tzz * g[2][i];
+        } else {
+            const TC txx = Te[q], tyy = Te[SH::NQ + q], txy = Te[2 * SH::NQ + q];
+            f[0][i] = txx * g[0][i] + txy * g[1][i];
+            f[1][i] = txy * g[0][i] + tyy * g[1][i];
+        }
+        s[i] = TC(0);
+    }
+    TC yl[D1];
+    bwd<DIM, D1, TC, false>(f, s, b0, b1, Bs, lane, yl);
+    store_line<DIM, D1, TC>(Ye + el * SH::NQ, lane, yl);
+    __syncthreads();
+    scatter_tile<DIM, D1, TC, TIO, OUT_JV>(P, t, tinf, Ye, y, v, halo);
+}
+
+// Load the geometric factors of one quadrature point.
+template <int DIM, typename T>
+__device__ __forceinline__ void load_geo(const double *__restrict__ ge, int NQ, int q, T (&M)[DIM == 3 ? 6 : 3],
+                                         T &iw, T &src)
+{
+    constexpr int NS = DIM == 3 ? 6 : 3;
+#pragma unroll
+    for (int c = 0; c < NS; ++c) M[c] = (T)ge[c * NQ + q];
+    iw = (T)ge[NS * NQ + q];
+    src = (T)ge[(NS + 1) * NQ + q];
+}
+
+// Residual R(u) (want_r) and/or the quadrature-point tangent J_D (T64 / T32), FP64.  The tangent
+// is the derivative part of the flux evaluated on dual numbers seeded with the unit directions of
+// the reference gradient (forward-mode AD at the quadrature point, Eq. 2).
+template <int DIM, int D1>
+__global__ void k_residual(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<double> Bs,
+                           const double *__restrict__ u, double *__restrict__ r, double *__restrict__ halo,
+                           double *__restrict__ T64, float *__restrict__ T32, int want_r)
+{
+    using SH = Shape<DIM, D1>;
+    using TC = double;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = P.T;
+    const int NE = DIM == 3 ? T * T * T : T * T;
+    TC *Vs = reinterpret_cast<TC *>(smem);
+    TC *bufs = Vs + pad4(P.S);
+    TC *Ye = bufs + NE * 6 * SH::NQ;
+    const int64_t t = blockIdx.x;
+    const TileInfo tinf = tile_info<DIM>(P, t);
+    load_slots<TC, double, false>(P, t, u, Vs);
+    __syncthreads();
+    const int el = threadIdx.x / SH::TEAM, lane = threadIdx.x % SH::TEAM;
+    int ec[3];
+    elem_coords<DIM>(el, T, ec);
+    TC *b0 = bufs + el * 6 * SH::NQ, *b1 = b0 + 3 * SH::NQ;
+    TC ul[D1];
+    gather_line<DIM, D1, TC>(P, Vs, ec, lane, ul);
+    TC g[DIM][D1];
+    fwd<DIM, D1, TC>(ul, b0, b1, Bs, lane, g);
+    const int64_t eint = t * NE + el;
+    const double *ge = P.geo + eint * (int64_t)(SH::NG * SH::NQ);
+    const double kr = P.kr ? P.kr[eint] : 1.0;
+    const bool want_t = (T64 != nullptr) || (T32 != nullptr);
+    TC f[DIM][D1], s[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        const int q = qidx<DIM, D1>(lane, i);
+        double M[SH::NS], iw, src;
+        load_geo<DIM, double>(ge, SH::NQ, q, M, iw, src);
+        s[i] = -src;
+        if (want_t) {
+            Dual<double, DIM> gd[DIM], qd[DIM];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                gd[d].v = g[d][i];
+#pragma unroll
+                for (int e = 0; e < DIM; ++e) gd[d].d[e] = (d == e) ? 1.0 : 0.0;
+            }
+            if constexpr (DIM == 3) flux3(gd, M, iw, kr, P.law, P.law_a, P.eps2, qd);
+            else flux2(gd, M, iw, kr, P.law, P.law_a, P.eps2, qd);
+            double tv[SH::NS];
+            if constexpr (DIM == 3) {
+                tv[0] = qd[0].d[0]; tv[1] = qd[1].d[1]; tv[2] = qd[2].d[2];
+                tv[3] = qd[0].d[1]; tv[4] = qd[0].d[2]; tv[5] = qd[1].d[2];
+            } else {
+                tv[0] = qd[0].d[0]; tv[1] = qd[1].d[1]; tv[2] = qd[0].d[1];
+            }
+            const int64_t tb = eint * (int64_t)(SH::NS * SH::NQ) + q;
+#pragma unroll
+            for (int c = 0; c < SH::NS; ++c) {
+                if (T64) T64[tb + c * SH::NQ] = tv[c];
+                if (T32) T32[tb + c * SH::NQ] = (float)tv[c];
+            }
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) f[d][i] = qd[d].v;
+        } else {
+            double gr[DIM], qr[DIM];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) gr[d] = g[d][i];
+            if constexpr (DIM == 3) flux3(gr, M, iw, kr, P.law, P.law_a, P.eps2, qr);
+            else flux2(gr, M, iw, kr, P.law, P.law_a, P.eps2, qr);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) f[d][i] = qr[d];
+        }
+    }
+    if (!want_r) return;   // uniform across the grid
+    TC yl[D1];
+    bwd<DIM, D1, TC, true>(f, s, b0, b1, Bs, lane, yl);
+    store_line<DIM, D1, TC>(Ye + el * SH::NQ, lane, yl);
+    __syncthreads();
+    scatter_tile<DIM, D1, TC, double, OUT_RES>(P, t, tinf, Ye, r, nullptr, halo);
+}
+
+// Stateless Jacobian action J(u) v: one dual direction seeded with the reference gradient of v.
+template <int DIM, int D1, typename TC, typename TIO>
+__global__ void k_jv_dual(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
+                          const double *__restrict__ u, const TIO *__restrict__ v, TIO *__restrict__ y,
+                          TC *__restrict__ halo)
+{
+    using SH = Shape<DIM, D1>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = P.T;
+    const int NE = DIM == 3 ? T * T * T : T * T;
+    TC *Vu = reinterpret_cast<TC *>(smem);
+    TC *Vv = Vu + pad4(P.S);
+    TC *bufs = Vv + pad4(P.S);
+    TC *Ye = bufs + NE * 6 * SH::NQ;
+    const int64_t t = blockIdx.x;
+    const TileInfo tinf = tile_info<DIM>(P, t);
+    load_slots<TC, double, false>(P, t, u, Vu);
+    load_slots<TC, TIO, true>(P, t, v, Vv);
+    __syncthreads();
+    const int el = threadIdx.x / SH::TEAM, lane = threadIdx.x % SH::TEAM;
+    int ec[3];
+    elem_coords<DIM>(el, T, ec);
+    TC *b0 = bufs + el * 6 * SH::NQ, *b1 = b0 + 3 * SH::NQ;
+    TC line[D1];
+    TC gu[DIM][D1], gv[DIM][D1];
+    gather_line<DIM, D1, TC>(P, Vu, ec, lane, line);
+    fwd<DIM, D1, TC>(line, b0, b1, Bs, lane, gu);
+    __syncthreads();
+    gather_line<DIM, D1, TC>(P, Vv, ec, lane, line);
+    fwd<DIM, D1, TC>(line, b0, b1, Bs, lane, gv);
+    const int64_t eint = t * NE + el;
+    const double *ge = P.geo + eint * (int64_t)(SH::NG * SH::NQ);
+    const TC kr = P.kr ? (TC)P.kr[eint] : TC(1);
+    TC f[DIM][D1], s[D1];
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        const int q = qidx<DIM, D1>(lane, i);
+        TC M[SH::NS], iw, src;
+        load_geo<DIM, TC>(ge, SH::NQ, q, M, iw, src);
+        Dual<TC, 1> gd[DIM], qd[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) { gd[d].v = gu[d][i]; gd[d].d[0] = gv[d][i]; }
+        if constexpr (DIM == 3) flux3(gd, M, iw, kr, P.law, (TC)P.law_a, (TC)P.eps2, qd);
+        else flux2(gd, M, iw, kr, P.law, (TC)P.law_a, (TC)P.eps2, qd);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) f[d][i] = qd[d].d[0];
+        s[i] = TC(0);
+    }
+    TC yl[D1];
+    bwd<DIM, D1, TC, false>(f, s, b0, b1, Bs, lane, yl);
+    store_line<DIM, D1, TC>(Ye + el * SH::NQ, lane, yl);
+    __syncthreads();
+    scatter_tile<DIM, D1, TC, TIO, OUT_JV>(P, t, tinf, Ye, y, v, halo);
+}
+
+// Jacobi diagonal diag(J)_l = sum_q sum_ab T_ab(q) dphi_l/dxi_a dphi_l/dxi_b, sum-factorised with
+// the squared / product 1D tables.
+template <int DIM, int D1, typename TC>
+__global__ void k_diag(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
+                       const TC *__restrict__ Tq, double *__restrict__ dg, TC *__restrict__ halo)
+{
+    using SH = Shape<DIM, D1>;
+    constexpr int NQ = SH::NQ;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = P.T;
+    const int NE = DIM == 3 ? T * T * T : T * T;
+    TC *bufs = reinterpret_cast<TC *>(smem) + pad4(P.S);
+    TC *Ye = bufs + NE * 6 * NQ;
+    const int64_t t = blockIdx.x;
+    const TileInfo tinf = tile_info<DIM>(P, t);
+    const int el = threadIdx.x / SH::TEAM, lane = threadIdx.x % SH::TEAM;
+    TC *b0 = bufs + el * 6 * NQ;
+    const TC *Te = Tq + (t * NE + el) * (int64_t)(SH::NS * NQ);
+    TC yl[D1];
+    if constexpr (DIM == 3) {
+        const int ti = lane % D1, tj = lane / D1;
+        TC tq[6][D1];
+#pragma unroll
+        for (int i = 0; i < D1; ++i) {
+            const int q = qidx<DIM, D1>(lane, i);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) tq[c][i] = Te[c * NQ + q];
+        }
+        // x: (qy,qz) = (ti,tj) -> six arrays [qz][qy][a]
+#pragma unroll
+        for (int a = 0; a < D1; ++a) {
+            TC I0 = 0, I1 = 0, I2 = 0, I3 = 0, I4 = 0, I5 = 0;
+#pragma unroll
+            for (int qx = 0; qx < D1; ++qx) {
+                const TC b2 = Bs.B2[qx * D1 + a], g2 = Bs.G2[qx * D1 + a], bg = Bs.BG[qx * D1 + a];
+                I0 += g2 * tq[0][qx];
+                I1 += b2 * tq[1][qx];
+                I2 += bg * (TC(2) * tq[3][qx]);
+                I3 += b2 * tq[2][qx];
+                I4 += bg * (TC(2) * tq[4][qx]);
+                I5 += b2 * (TC(2) * tq[5][qx]);
+            }
+            const int o = (tj * D1 + ti) * D1 + a;
+            b0[o] = I0; b0[NQ + o] = I1; b0[2 * NQ + o] = I2;
+            b0[3 * NQ + o] = I3; b0[4 * NQ + o] = I4; b0[5 * NQ + o] = I5;
+        }
+        __syncthreads();
+        // y: (a, qz) = (ti, tj)
+        TC in[6][D1];
+#pragma unroll
+        for (int qy = 0; qy < D1; ++qy)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) in[c][qy] = b0[c * NQ + (tj * D1 + qy) * D1 + ti];
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < D1; ++b) {
+            TC Z0 = 0, Z1 = 0, Z2 = 0;
+#pragma unroll
+            for (int qy = 0; qy < D1; ++qy) {
+                const TC b2 = Bs.B2[qy * D1 + b], g2 = Bs.G2[qy * D1 + b], bg = Bs.BG[qy * D1 + b];
+                Z0 += b2 * in[0][qy] + g2 * in[1][qy] + bg * in[2][qy];
+                Z1 += b2 * in[3][qy];
+                Z2 += b2 * in[4][qy] + bg * in[5][qy];
+            }
+            const int o = (tj * D1 + b) * D1 + ti;
+            b0[o] = Z0; b0[NQ + o] = Z1; b0[2 * NQ + o] = Z2;
+        }
+        __syncthreads();
+        // z: (a, b) = (ti, tj)
+        TC z[3][D1];
+#pragma unroll
+        for (int qz = 0; qz < D1; ++qz)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) z[c][qz] = b0[c * NQ + (qz * D1 + tj) * D1 + ti];
+#pragma unroll
+        for (int c = 0; c < D1; ++c) {
+            TC acc = 0;
+#pragma unroll
+            for (int qz = 0; qz < D1; ++qz)
+                acc += Bs.B2[qz * D1 + c] * z[0][qz] + Bs.G2[qz * D1 + c] * z[1][qz] + Bs.BG[qz * D1 + c] * z[2][qz];
+            yl[c] = acc;
+        }
+    } else {
+        TC tq[3][D1];
+#pragma unroll
+        for (int i = 0; i < D1; ++i) {
+            const int q = qidx<DIM, D1>(lane, i);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tq[c][i] = Te[c * NQ + q];
+        }
+        // y: thread qx = lane -> [b][qx]
+#pragma unroll
+        for (int b = 0; b < D1; ++b) {
+            TC I1 = 0, I2 = 0, I3 = 0;
+#pragma unroll
+            for (int qy = 0; qy < D1; ++qy) {
+                I1 += Bs.B2[qy * D1 + b] * tq[0][qy];
+                I2 += Bs.G2[qy * D1 + b] * tq[1][qy];
+                I3 += Bs.BG[qy * D1 + b] * (TC(2) * tq[2][qy]);
+            }
+            b0[b * D1 + lane] = I1; b0[NQ + b * D1 + lane] = I2; b0[2 * NQ + b * D1 + lane] = I3;
+        }
+        __syncthreads();
+        // x: thread b = lane
+#pragma unroll
+        for (int a = 0; a < D1; ++a) {
+            TC acc = 0;
+#pragma unroll
+            for (int qx = 0; qx < D1; ++qx)
+                acc += Bs.G2[qx * D1 + a] * b0[lane * D1 + qx] + Bs.B2[qx * D1 + a] * b0[NQ + lane * D1 + qx] +
+                       Bs.BG[qx * D1 + a] * b0[2 * NQ + lane * D1 + qx];
+            yl[a] = acc;
+        }
+    }
+    store_line<DIM, D1, TC>(Ye + el * NQ, lane, yl);
+    __syncthreads();
+    scatter_tile<DIM, D1, TC, double, OUT_DIAG>(P, t, tinf, Ye, dg, nullptr, halo);
+}
+
+// Adjoint design gradient: grad[e] = lambda_e^T dr_e/drho_e, with d/drho taken by a dual number
+// seeded on kappa_rho (derivative kappa_rho'(rho_e)) at each quadrature point; element-local sum.
+template <int DIM, int D1>
+__global__ void k_vjp(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<double> Bs,
+                      const double *__restrict__ u, const double *__restrict__ lam, double *__restrict__ grad)
+{
+    using SH = Shape<DIM, D1>;
+    using TC = double;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = P.T;
+    const int NE = DIM == 3 ? T * T * T : T * T;
+    TC *Vu = reinterpret_cast<TC *>(smem);
+    TC *Vl = Vu + pad4(P.S);
+    TC *bufs = Vl + pad4(P.S);
+    TC *red = bufs + NE * 6 * SH::NQ;
+    const int64_t t = blockIdx.x;
+    const TileInfo tinf = tile_info<DIM>(P, t);
+    load_slots<TC, double, false>(P, t, u, Vu);
+    load_slots<TC, double, true>(P, t, lam, Vl);
+    __syncthreads();
+    const int el = threadIdx.x / SH::TEAM, lane = threadIdx.x % SH::TEAM;
+    int ec[3];
+    elem_coords<DIM>(el, T, ec);
+    TC *b0 = bufs + el * 6 * SH::NQ, *b1 = b0 + 3 * SH::NQ;
+    TC line[D1];
+    TC gu[DIM][D1], gl[DIM][D1];
+    gather_line<DIM, D1, TC>(P, Vu, ec, lane, line);
+    fwd<DIM, D1, TC>(line, b0, b1, Bs, lane, gu);
+    __syncthreads();
+    gather_line<DIM, D1, TC>(P, Vl, ec, lane, line);
+    fwd<DIM, D1, TC>(line, b0, b1, Bs, lane, gl);
+    const int64_t eint = t * NE + el;
+    const double *ge = P.geo + eint * (int64_t)(SH::NG * SH::NQ);
+    Dual<double, 1> kr;
+    kr.v = P.kr ? P.kr[eint] : 1.0;
+    kr.d[0] = P.dkr ? P.dkr[eint] : 0.0;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < D1; ++i) {
+        const int q = qidx<DIM, D1>(lane, i);
+        double M[SH::NS], iw, src;
+        load_geo<DIM, double>(ge, SH::NQ, q, M, iw, src);
+        Dual<double, 1> gd[DIM], qd[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) { gd[d].v = gu[d][i]; gd[d].d[0] = 0.0; }
+        if constexpr (DIM == 3) flux3(gd, M, iw, kr, P.law, P.law_a, P.eps2, qd);
+        else flux2(gd, M, iw, kr, P.law, P.law_a, P.eps2, qd);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) acc += gl[d][i] * qd[d].d[0];
+    }
+    red[el * SH::TEAM + lane] = acc;
+    __syncthreads();
+    if (lane == 0 && elem_valid<DIM>(tinf, ec)) {
+        double sum = 0.0;
+        for (int j = 0; j < SH::TEAM; ++j) sum += red[el * SH::TEAM + j];
+        grad[elem_public<DIM>(P, tinf, ec)] = sum;
+    }
+}
+
+// --------------------------------------------------------------------------------------------
+// Host launchers of one (dim, order) instantiation
+// --------------------------------------------------------------------------------------------
+template <typename K>
+inline cudaError_t raise_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int DIM, int D1>
+struct Ops {
+    using SH = Shape<DIM, D1>;
+    static int nthreads(const fe_ctx *c) { return c->NE * SH::TEAM; }
+
+    template <typename TC, typename TIO>
+    static void fixup(fe_ctx *c, TIO *y, cudaStream_t st)
+    {
+        if (c->nfix == 0) return;
+        LaunchScope ls(c, "fixup", st);
+        const int bs = 256;
+        const int64_t nb = (c->nfix + bs - 1) / bs;
+        k_fixup<TC, TIO><<<(unsigned)nb, bs, 0, st>>>(c->fix, reinterpret_cast<TC *>(c->d_halo), y);
+    }
+
+    static void residual(fe_ctx *c, const double *u, double *r, double *T64, float *T32, cudaStream_t st)
+    {
+        const size_t sm = smem_bytes<DIM, D1>(c->S, c->T, sizeof(double), 1);
+        {
+            LaunchScope ls(c, r ? "residual" : "linearize", st);
+            k_residual<DIM, D1><<<(unsigned)c->ntiles, nthreads(c), sm, st>>>(
+                c->op, c->b64, u, r, reinterpret_cast<double *>(c->d_halo), T64, T32, r != nullptr);
+        }
+        if (r) fixup<double, double>(c, r, st);
+    }
+
+    template <typename TC, typename TIO>
+    static void jv_pa(fe_ctx *c, const TIO *v, TIO *y, cudaStream_t st)
+    {
+        const size_t sm = smem_bytes<DIM, D1>(c->S, c->T, sizeof(TC), 1);
+        const TC *Tq;
+        const BasisT<TC> *bs;
+        if constexpr (sizeof(TC) == 8) { Tq = reinterpret_cast<const TC *>(c->d_T64); bs = reinterpret_cast<const BasisT<TC> *>(&c->b64); }
+        else { Tq = reinterpret_cast<const TC *>(c->d_T32); bs = reinterpret_cast<const BasisT<TC> *>(&c->b32); }
+        {
+            LaunchScope ls(c, sizeof(TC) == 8 ? "jv_pa_f64" : "jv_pa_f32", st);
+            k_jv_pa<DIM, D1, TC, TIO><<<(unsigned)c->ntiles, nthreads(c), sm, st>>>(
+                c->op, *bs, Tq, v, y, reinterpret_cast<TC *>(c->d_halo));
+        }
+        fixup<TC, TIO>(c, y, st);
+    }
+    static void jv_pa_64(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<double, double>(c, v, y, st); }
+    static void jv_pa_32(fe_ctx *c, const float *v, float *y, cudaStream_t st) { jv_pa<float, float>(c, v, y, st); }
+    static void jv_pa_32d(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<float, double>(c, v, y, st); }
+
+    template <typename TC, typename TIO>
+    static void jv_dual(fe_ctx *c, const double *u, const TIO *v, TIO *y, cudaStream_t st)
+    {
+        const size_t sm = smem_bytes<DIM, D1>(c->S, c->T, sizeof(TC), 2);
+        const BasisT<TC> *bs;
+        if constexpr (sizeof(TC) == 8) bs = reinterpret_cast<const BasisT<TC> *>(&c->b64);
+        else bs = reinterpret_cast<const BasisT<TC> *>(&c->b32);
+        {
+            LaunchScope ls(c, sizeof(TC) == 8 ? "jv_dual_f64" : "jv_dual_f32", st);
+            k_jv_dual<DIM, D1, TC, TIO><<<(unsigned)c->ntiles, nthreads(c), sm, st>>>(
+                c->op, *bs, u, v, y, reinterpret_cast<TC *>(c->d_halo));
+        }
+        fixup<TC, TIO>(c, y, st);
+    }
+    static void jv_dual_64(fe_ctx *c, const double *u, const double *v, double *y, cudaStream_t st) { jv_dual<double, double>(c, u, v, y, st); }
+    static void jv_dual_32(fe_ctx *c, const double *u, const float *v, float *y, cudaStream_t st) { jv_dual<float, float>(c, u, v, y, st); }
+    static void jv_dual_32d(fe_ctx *c, const double *u, const double *v, double *y, cudaStream_t st) { jv_dual<float, double>(c, u, v, y, st); }
+
+    template <typename TC>
+    static void diag(fe_ctx *c, double *d, cudaStream_t st)
+    {
+        const size_t sm = smem_bytes<DIM, D1>(c->S, c->T, sizeof(TC), 0) + sizeof(TC) * pad4(c->S);
+        const TC *Tq;
+        const BasisT<TC> *bs;
+        if constexpr (sizeof(TC) == 8) { Tq = reinterpret_cast<const TC *>(c->d_T64); bs = reinterpret_cast<const BasisT<TC> *>(&c->b64); }
+        else { Tq = reinterpret_cast<const TC *>(c->d_T32); bs = reinterpret_cast<const BasisT<TC> *>(&c->b32); }
+        {
+            LaunchScope ls(c, "diag", st);
+            k_diag<DIM, D1, TC><<<(unsigned)c->ntiles, nthreads(c), sm, st>>>(c->op, *bs, Tq, d,
+                                                                              reinterpret_cast<TC *>(c->d_halo));
+        }
+        fixup<TC, double>(c, d, st);
+    }
+    static void diag_64(fe_ctx *c, double *d, cudaStream_t st) { diag<double>(c, d, st); }
+    static void diag_32(fe_ctx *c, double *d, cudaStream_t st) { diag<float>(c, d, st); }
+
+    static void vjp(fe_ctx *c, const double *u, const double *lam, double *grad, cudaStream_t st)
+    {
+        const size_t sm = smem_bytes<DIM, D1>(c->S, c->T, sizeof(double), 2);
+        LaunchScope ls(c, "adjoint_vjp", st);
+        k_vjp<DIM, D1><<<(unsigned)c->ntiles, nthreads(c), sm, st>>>(c->op, c->b64, u, lam, grad);
+    }
+
+    static size_t max_smem(int S, int T) { return smem_bytes<DIM, D1>(S, T, sizeof(double), 2) + 8 * pad4(S); }
+
+    static cudaError_t prepare(fe_ctx *c)
+    {
+        const size_t s1d = smem_bytes<DIM, D1>(c->S, c->T, sizeof(double), 1);
+        const size_t s1f = smem_bytes<DIM, D1>(c->S, c->T, sizeof(float), 1);
+        const size_t s2d = smem_bytes<DIM, D1>(c->S, c->T, sizeof(double), 2);
+        const size_t s2f = smem_bytes<DIM, D1>(c->S, c->T, sizeof(float), 2);
+        cudaError_t e = cudaSuccess, e2;
+#define FEOD_RAISE(k, b) if ((e2 = raise_smem(k, b)) != cudaSuccess) e = e2
+        FEOD_RAISE((k_residual<DIM, D1>), s1d);
+        FEOD_RAISE((k_jv_pa<DIM, D1, double, double>), s1d);
+        FEOD_RAISE((k_jv_pa<DIM, D1, float, float>), s1f);
+        FEOD_RAISE((k_jv_pa<DIM, D1, float, double>), s1f);
+        FEOD_RAISE((k_jv_dual<DIM, D1, double, double>), s2d);
+        FEOD_RAISE((k_jv_dual<DIM, D1, float, float>), s2f);
+        FEOD_RAISE((k_jv_dual<DIM, D1, float, double>), s2f);
+        FEOD_RAISE((k_diag<DIM, D1, double>), s1d);
+        FEOD_RAISE((k_diag<DIM, D1, float>), s1f);
+        FEOD_RAISE((k_vjp<DIM, D1>), s2d);
+#undef FEOD_RAISE
+        return e;
+    }
+
+    static const OpTable *table()
+    {
+        static const OpTable t = { DIM, D1, residual, jv_pa_64, jv_pa_32, jv_pa_32d,
+                                   jv_dual_64, jv_dual_32, jv_dual_32d, diag_64, diag_32, vjp,
+                                   prepare, max_smem };
+        return &t;
+    }
+};
+
+}  // namespace feod

@@ -1,0 +1,187 @@
+// internal.h -- context, kernel parameter blocks and the per-(dim, order) dispatch table of the
+// FEOD library.  Not part of the public ABI (include/feod.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/feod.h"
+
+namespace feod {
+
+constexpr int MAXQ = 7;                 // points per direction: order 6 -> 7 nodes / Gauss points
+constexpr int MAX_ORDER = 6;
+
+// Slot code of a tile slot: bits 0..29 global DOF, bit 30 essential, bit 31 halo (the slot's DOF
+// is owned by a neighbouring tile; this tile's partial sum goes to the halo buffer).
+constexpr uint32_t SLOT_GMASK = 0x3FFFFFFFu;
+constexpr uint32_t SLOT_ESS = 0x40000000u;
+constexpr uint32_t SLOT_HALO = 0x80000000u;
+constexpr uint32_t SLOT_INVALID = 0xFFFFFFFFu;
+constexpr int64_t MAX_DOFS = (int64_t)SLOT_GMASK;   // 2^30 - 1
+
+// 1D basis tables on the reference interval [0,1], row-major [q][a] with q < Q1, a < D1:
+// B = phi_a(xi_q), G = phi_a'(xi_q), and the products used by the Jacobi diagonal.
+template <typename T>
+struct BasisT {
+    T B[MAXQ * MAXQ];
+    T G[MAXQ * MAXQ];
+    T B2[MAXQ * MAXQ];   // B^2
+    T G2[MAXQ * MAXQ];   // G^2
+    T BG[MAXQ * MAXQ];   // B*G
+};
+
+// Pointwise law kinds (uniform for a launch): kappa(base) = base^a with a = (p-2)/2.
+enum LawKind : int { LAW_GENERIC = 0, LAW_P2 = 1, LAW_P3 = 2, LAW_P4 = 3 };
+
+// Everything the element kernels need about the mesh, tiling and law.
+struct OpParams {
+    int n;            // elements per direction
+    int T;            // tile edge in elements
+    int nt;           // tiles per direction
+    int S;            // slots per tile = (k T + 1)^dim
+    int SE;           // slots per tile edge = k T + 1
+    int law;          // LawKind
+    int64_t ntiles;
+    const uint32_t *slot;   // [ntiles][S]
+    const double *geo;      // [nepad][NG][NQ]
+    const double *kr;       // [nepad] kappa_rho per element (internal order) or nullptr
+    const double *dkr;      // [nepad] kappa_rho' per element or nullptr
+    const int *skip;        // if non-null and *skip != 0 the kernel returns at once (CG batches)
+    double law_a;     // (p-2)/2
+    double eps2;      // eps^2
+};
+
+// Fix-up (deterministic G^T across tiles): y[fix_g[r]] += sum_j halo[fix_h[j]], j in [off[r], off[r+1])
+struct FixParams {
+    int64_t nfix;
+    const uint32_t *fix_g;
+    const uint32_t *fix_off;
+    const uint32_t *fix_h;
+    const int *skip;
+};
+
+// Geometry setup parameters.
+struct GeomParams {
+    int dim, d1, q1, n, T, nt;
+    int64_t nepad;
+    double xq[MAXQ], wq[MAXQ];     // Gauss points / weights on [0,1]
+    double xn[MAXQ];               // GLL nodes on [0,1]
+    int f_kind;
+    double f_const;
+    double p;
+};
+
+// Launchers of one (dim, order) instantiation.  Each runs the element kernel and, where the
+// kernel assembles a global vector, the halo fix-up, on `st`.
+struct OpTable {
+    int dim, d1;
+    // residual (want_r) and/or quadrature-point tangent (T64 / T32 non-null) of u
+    void (*residual)(fe_ctx *c, const double *u, double *r, double *T64, float *T32, cudaStream_t st);
+    // partially assembled J v
+    void (*jv_pa_64)(fe_ctx *c, const double *v, double *y, cudaStream_t st);
+    void (*jv_pa_32)(fe_ctx *c, const float *v, float *y, cudaStream_t st);
+    void (*jv_pa_32d)(fe_ctx *c, const double *v, double *y, cudaStream_t st);
+    // stateless J(u) v with one dual direction
+    void (*jv_dual_64)(fe_ctx *c, const double *u, const double *v, double *y, cudaStream_t st);
+    void (*jv_dual_32)(fe_ctx *c, const double *u, const float *v, float *y, cudaStream_t st);
+    void (*jv_dual_32d)(fe_ctx *c, const double *u, const double *v, double *y, cudaStream_t st);
+    // Jacobi diagonal from the stored tangent
+    void (*diag_64)(fe_ctx *c, double *d, cudaStream_t st);
+    void (*diag_32)(fe_ctx *c, double *d, cudaStream_t st);
+    // adjoint design gradient
+    void (*vjp)(fe_ctx *c, const double *u, const double *lam, double *grad, cudaStream_t st);
+    // raise the dynamic shared-memory limit of every kernel for this context's tile size
+    // (called once at setup, so that no attribute call happens inside a graph capture)
+    cudaError_t (*prepare)(fe_ctx *c);
+    // bytes of dynamic shared memory of the largest kernel for tile size T
+    size_t (*max_smem)(int S, int T);
+};
+
+const OpTable *find_ops(int dim, int d1);
+
+}  // namespace feod
+
+// The context.  Owns all device memory it allocates.
+struct fe_ctx {
+    int dim = 0, n = 0, k = 0, d1 = 0, q1 = 0;
+    int T = 0, nt = 0, S = 0, SE = 0, NE = 0;   // tiling
+    int NQ = 0, NS = 0, NG = 0;                 // points per element, sym entries, geo comps
+    int64_t nl = 0, nfree = 0, ne = 0, nepad = 0, ntiles = 0;
+    int device = 0;
+    int num_sms = 0;
+
+    // problem
+    double p = 3.0, eps = 0.0, kappa_eps = 0.0, kappa_q = 1.0, f_const = 0.0;
+    int f_kind = 0, law = 0;
+    bool has_rho = false;
+
+    // device arrays
+    uint32_t *d_slot = nullptr;
+    uint32_t *d_fix_g = nullptr, *d_fix_off = nullptr, *d_fix_h = nullptr;
+    int64_t nfix = 0, nfixh = 0;
+    double *d_vert = nullptr;
+    double *d_geo = nullptr;
+    double *d_rho = nullptr;      // public order
+    double *d_kr = nullptr, *d_dkr = nullptr;   // internal order
+    double *d_T64 = nullptr;
+    float *d_T32 = nullptr;
+    double *d_diag = nullptr;
+    void *d_halo = nullptr;       // ntiles*S*8 bytes
+    int *d_err = nullptr;
+    bool lin64 = false, lin32 = false, have_diag = false;
+
+    // Newton / CG work space (allocated on first use)
+    double *w_r = nullptr, *w_d = nullptr, *w_trial = nullptr, *w_dinv = nullptr;
+    double *w_cx = nullptr, *w_cr = nullptr, *w_cp = nullptr, *w_cq = nullptr;
+    void *w_state = nullptr;      // device CG state
+    double *w_partial = nullptr;  // reduction partials
+    void *h_state = nullptr;      // pinned host mirror
+    cudaStream_t own_stream = nullptr;
+    // captured CG batches, [0] FP64 operator, [1] FP32 operator with FP64 vectors
+    cudaGraphExec_t cg_exec[2] = { nullptr, nullptr };
+    int cg_batch[2] = { 0, 0 };
+    int64_t cg_launches[2] = { 0, 0 };
+
+    feod::OpParams op{};
+    feod::FixParams fix{};
+    feod::BasisT<double> b64{};
+    feod::BasisT<float> b32{};
+    feod::GeomParams gp{};
+    const feod::OpTable *ops = nullptr;
+
+    // profiling / counting
+    bool prof = false;
+    int64_t launches = 0;
+    struct ProfRec { int name; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<std::string> prof_names;
+    std::vector<int64_t> prof_count;
+    std::vector<double> prof_ms;
+
+    int64_t mem_bytes = 0;
+    std::string err;
+};
+
+namespace feod {
+
+// Profiling bracket around one kernel launch.
+int prof_name_id(fe_ctx *c, const char *name);
+void prof_begin(fe_ctx *c, int name_id, cudaStream_t st, cudaEvent_t *a);
+void prof_end(fe_ctx *c, int name_id, cudaStream_t st, cudaEvent_t a);
+
+struct LaunchScope {
+    fe_ctx *c; int id; cudaStream_t st; cudaEvent_t a = nullptr;
+    LaunchScope(fe_ctx *c_, const char *name, cudaStream_t st_) : c(c_), st(st_) {
+        c->launches++;
+        id = c->prof ? prof_name_id(c, name) : -1;
+        if (c->prof) prof_begin(c, id, st, &a);
+    }
+    ~LaunchScope() { if (c->prof) prof_end(c, id, st, a); }
+};
+
+}  // namespace feod

@@ -1,0 +1,326 @@
+// vector_kernels.cu -- setup kernels (geometry factors, DOF coordinates, design factors) and the
+// FP64 vector kernels of the Newton-CG solver: deterministic dot products (fixed grid, fixed
+// two-level tree, last-block finalisation) and fused CG updates whose scalars stay on the device.
+#include <cmath>
+
+#include "vector_kernels.h"
+
+namespace feod {
+
+// ------------------------------------------------------------------------------------------------
+// Setup: geometric factors at every quadrature point (one thread per point)
+// ------------------------------------------------------------------------------------------------
+// Element map x(xi) = sum over corners of prod_d (xi_d or 1 - xi_d) X_corner on [0,1]^dim.
+// Stored per element (internal tile order) and component: M = w detJ J^-1 J^-T (symmetric,
+// 3D xx yy zz xy xz yz / 2D xx yy xy), 1/(w detJ), w detJ f(x).
+__global__ void k_geometry(const GeomParams G, const double *__restrict__ vert, double *__restrict__ geo,
+                           int *__restrict__ err)
+{
+    const int dim = G.dim, q1 = G.q1;
+    const int nq = dim == 3 ? q1 * q1 * q1 : q1 * q1;
+    const int ns = dim == 3 ? 6 : 3, ng = ns + 2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= G.nepad * nq) return;
+    const int64_t eint = idx / nq;
+    const int q = (int)(idx % nq);
+    const int NE = dim == 3 ? G.T * G.T * G.T : G.T * G.T;
+    const int64_t t = eint / NE;
+    const int el = (int)(eint % NE);
+    int ec[3] = { el % G.T, (el / G.T) % G.T, dim == 3 ? el / (G.T * G.T) : 0 };
+    int64_t tr = t;
+    int64_t ex[3] = { 0, 0, 0 };
+    bool valid = true;
+    for (int d = 0; d < dim; ++d) {
+        const int64_t Tc = tr % G.nt; tr /= G.nt;
+        ex[d] = Tc * G.T + ec[d];
+        if (ex[d] >= G.n) valid = false;
+    }
+    double *ge = geo + eint * (int64_t)(ng * nq);
+    if (!valid) {
+        for (int c = 0; c < ng; ++c) ge[c * nq + q] = 0.0;
+        return;
+    }
+    const int qi[3] = { q % q1, (q / q1) % q1, dim == 3 ? q / (q1 * q1) : 0 };
+    double xi[3] = { G.xq[qi[0]], G.xq[qi[1]], dim == 3 ? G.xq[qi[2]] : 0.0 };
+    double w = G.wq[qi[0]] * G.wq[qi[1]] * (dim == 3 ? G.wq[qi[2]] : 1.0);
+    const int64_t nv = G.n + 1;
+    double J[3][3] = { { 0, 0, 0 }, { 0, 0, 0 }, { 0, 0, 0 } }, x[3] = { 0, 0, 0 };
+    const int ncorner = dim == 3 ? 8 : 4;
+    for (int c = 0; c < ncorner; ++c) {
+        const int cb[3] = { c & 1, (c >> 1) & 1, (c >> 2) & 1 };
+        const int64_t vi = (ex[0] + cb[0]) + nv * ((ex[1] + cb[1]) + (dim == 3 ? nv * (ex[2] + cb[2]) : 0));
+        double sh[3], dsh[3];
+        for (int d = 0; d < 3; ++d) {
+            sh[d] = d < dim ? (cb[d] ? xi[d] : 1.0 - xi[d]) : 1.0;
+            dsh[d] = cb[d] ? 1.0 : -1.0;
+        }
+        for (int a = 0; a < dim; ++a) {
+            const double X = vert[vi * dim + a];
+            x[a] += sh[0] * sh[1] * sh[2] * X;
+            J[a][0] += dsh[0] * sh[1] * sh[2] * X;
+            J[a][1] += sh[0] * dsh[1] * sh[2] * X;
+            if (dim == 3) J[a][2] += sh[0] * sh[1] * dsh[2] * X;
+        }
+    }
+    double det, Mt[6];
+    if (dim == 3) {
+        // cofactor matrix C; J^-1 = C^T / det, so J^-1 J^-T = C^T C / det^2
+        double C[3][3];
+        C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+        // (J^-1 J^-T)_ab = sum_c (J^-1)_ac (J^-1)_bc = sum_c C_ca C_cb / det^2
+        const int pa[6] = { 0, 1, 2, 0, 0, 1 }, pb[6] = { 0, 1, 2, 1, 2, 2 };
+        for (int m = 0; m < 6; ++m) {
+            double s = 0.0;
+            for (int c = 0; c < 3; ++c) s += C[c][pa[m]] * C[c][pb[m]];
+            Mt[m] = s;
+        }
+    } else {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        // J^-1 = [[J11, -J01], [-J10, J00]] / det
+        const double i00 = J[1][1], i01 = -J[0][1], i10 = -J[1][0], i11 = J[0][0];
+        Mt[0] = i00 * i00 + i01 * i01;
+        Mt[1] = i10 * i10 + i11 * i11;
+        Mt[2] = i00 * i10 + i01 * i11;
+    }
+    if (!(det > 0.0)) {
+        atomicExch(err, 1);
+        for (int c = 0; c < ng; ++c) ge[c * nq + q] = 0.0;
+        return;
+    }
+    const double wdet = w * det;
+    const double scale = wdet / (det * det);       // w detJ / det^2
+    for (int m = 0; m < ns; ++m) ge[m * nq + q] = scale * Mt[m];
+    ge[ns * nq + q] = 1.0 / wdet;
+    double f;
+    if (G.f_kind == 0) {
+        f = G.f_const;
+    } else {
+        // source of the manufactured solution u* = exp(a.x), a = (1, 1/2, 1/3):
+        // -div(|grad u*|^{p-2} grad u*) = -(p-1) |a|^p exp((p-1) a.x)
+        const double a[3] = { 1.0, 0.5, 1.0 / 3.0 };
+        double ax = 0.0, a2 = 0.0;
+        for (int d = 0; d < dim; ++d) { ax += a[d] * x[d]; a2 += a[d] * a[d]; }
+        f = -(G.p - 1.0) * pow(a2, 0.5 * G.p) * exp((G.p - 1.0) * ax);
+    }
+    ge[(ns + 1) * nq + q] = wdet * f;
+}
+
+// Physical coordinates of every DOF (the element map at the GLL node), device [nl][dim].
+__global__ void k_node_coords(const GeomParams G, int k, const double *__restrict__ vert, double *__restrict__ xyz,
+                              int64_t nl)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nl) return;
+    const int dim = G.dim;
+    const int64_t m = (int64_t)k * G.n + 1, nv = G.n + 1;
+    int64_t gi[3] = { g % m, (g / m) % m, dim == 3 ? g / (m * m) : 0 };
+    int64_t ex[3] = { 0, 0, 0 };
+    double xi[3] = { 0, 0, 0 };
+    for (int d = 0; d < dim; ++d) {
+        int64_t e = gi[d] / k;
+        if (e >= G.n) e = G.n - 1;
+        ex[d] = e;
+        xi[d] = G.xn[gi[d] - k * e];
+    }
+    double x[3] = { 0, 0, 0 };
+    for (int c = 0; c < (dim == 3 ? 8 : 4); ++c) {
+        const int cb[3] = { c & 1, (c >> 1) & 1, (c >> 2) & 1 };
+        const int64_t vi = (ex[0] + cb[0]) + nv * ((ex[1] + cb[1]) + (dim == 3 ? nv * (ex[2] + cb[2]) : 0));
+        double sh = 1.0;
+        for (int d = 0; d < dim; ++d) sh *= cb[d] ? xi[d] : 1.0 - xi[d];
+        for (int a = 0; a < dim; ++a) x[a] += sh * vert[vi * dim + a];
+    }
+    for (int a = 0; a < dim; ++a) xyz[g * dim + a] = x[a];
+}
+
+// kappa_rho(rho) = kappa_eps + rho^kappa_q and its derivative, per element in internal order.
+__global__ void k_design_factors(const GeomParams G, const double *__restrict__ rho, double kappa_eps,
+                                 double kappa_q, double *__restrict__ kr, double *__restrict__ dkr)
+{
+    const int64_t eint = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (eint >= G.nepad) return;
+    const int dim = G.dim;
+    const int NE = dim == 3 ? G.T * G.T * G.T : G.T * G.T;
+    const int64_t t = eint / NE;
+    const int el = (int)(eint % NE);
+    int ec[3] = { el % G.T, (el / G.T) % G.T, dim == 3 ? el / (G.T * G.T) : 0 };
+    int64_t tr = t, ex[3] = { 0, 0, 0 };
+    bool valid = true;
+    for (int d = 0; d < dim; ++d) {
+        const int64_t Tc = tr % G.nt; tr /= G.nt;
+        ex[d] = Tc * G.T + ec[d];
+        if (ex[d] >= G.n) valid = false;
+    }
+    if (!valid) { kr[eint] = 1.0; dkr[eint] = 0.0; return; }
+    const int64_t e = ex[0] + G.n * (ex[1] + (dim == 3 ? (int64_t)G.n * ex[2] : 0));
+    const double r = rho[e];
+    kr[eint] = kappa_eps + pow(r, kappa_q);
+    dkr[eint] = kappa_q * pow(r, kappa_q - 1.0);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Deterministic reductions
+// ------------------------------------------------------------------------------------------------
+// Block sum of `v` over RED_THREADS threads in a fixed tree; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+// The last block to finish (ticket counter) sums the per-block partials in a fixed order.
+// Returns true in every thread of that block; *out receives the NSUM sums in thread 0.
+template <int NSUM>
+__device__ __forceinline__ bool last_block_sum(double (&mine)[NSUM], double *partial, unsigned *counter,
+                                               double (&out)[NSUM], double *sh)
+{
+    __shared__ bool is_last;
+    for (int k = 0; k < NSUM; ++k) {
+        const double b = block_sum(mine[k], sh);
+        if (threadIdx.x == 0) partial[k * RED_BLOCKS + blockIdx.x] = b;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    for (int k = 0; k < NSUM; ++k) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += RED_THREADS)
+            v += ((volatile double *)partial)[k * RED_BLOCKS + i];
+        out[k] = block_sum(v, sh);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+__global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                      double *partial, unsigned *counter, double *out)
+{
+    __shared__ double sh[RED_THREADS];
+    double s[1] = { 0.0 };
+    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS)
+        s[0] += a[i] * b[i];
+    double r[1];
+    if (last_block_sum<1>(s, partial, counter, r, sh) && threadIdx.x == 0) *out = r[0];
+}
+
+// CG start (x = 0): r = b, p = z = dinv b; rz = r.z, rr = r.r; tol2 = rtol^2 rr.
+__global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, double *__restrict__ x,
+                          double *__restrict__ r, double *__restrict__ p, int64_t n, CgState *st, double rtol,
+                          int max_iter, double *partial)
+{
+    __shared__ double sh[RED_THREADS];
+    double s[2] = { 0.0, 0.0 };
+    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+        const double bi = b[i], zi = dinv[i] * bi;
+        x[i] = 0.0; r[i] = bi; p[i] = zi;
+        s[0] += bi * zi; s[1] += bi * bi;
+    }
+    double o[2];
+    if (last_block_sum<2>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+        st->rz = o[0]; st->rr = o[1]; st->rr0 = o[1];
+        st->tol2 = rtol * rtol * o[1];
+        st->iter = 0; st->max_iter = max_iter;
+        st->done = (o[1] <= st->tol2 || o[1] == 0.0) ? CG_CONVERGED : (isfinite(o[1]) ? 0 : CG_NAN);
+        if (max_iter <= 0 && !st->done) st->done = CG_MAXIT;
+    }
+}
+
+// alpha = rz / (p.q); breakdown when p.q <= 0 or not finite.
+__global__ void k_cg_alpha(const double *__restrict__ p, const double *__restrict__ q, int64_t n, CgState *st,
+                           double *partial)
+{
+    if (st->done) return;
+    __shared__ double sh[RED_THREADS];
+    double s[1] = { 0.0 };
+    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS)
+        s[0] += p[i] * q[i];
+    double o[1];
+    if (last_block_sum<1>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+        st->pq = o[0];
+        if (!(o[0] > 0.0) || !isfinite(o[0])) { st->done = CG_BREAKDOWN; st->alpha = 0.0; }
+        else st->alpha = st->rz / o[0];
+    }
+}
+
+// x += alpha p; r -= alpha q; z = dinv r; rz' = r.z, rr = r.r; beta = rz'/rz; convergence test.
+__global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                            const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, CgState *st,
+                            double *partial)
+{
+    if (st->done) return;
+    __shared__ double sh[RED_THREADS];
+    const double alpha = st->alpha;
+    double s[2] = { 0.0, 0.0 };
+    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        s[0] += ri * dinv[i] * ri; s[1] += ri * ri;
+    }
+    double o[2];
+    if (last_block_sum<2>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+        st->beta = o[0] / st->rz;
+        st->rz = o[0]; st->rr = o[1];
+        st->iter += 1;
+        if (!isfinite(o[1])) st->done = CG_NAN;
+        else if (o[1] <= st->tol2) st->done = CG_CONVERGED;
+        else if (st->iter >= st->max_iter) st->done = CG_MAXIT;
+    }
+}
+
+// p = dinv r + beta p (skipped once converged).
+__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
+                               int64_t n, const CgState *st)
+{
+    if (st->done) return;
+    const double beta = st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = dinv[i] * r[i] + beta * p[i];
+}
+
+// y = a + alpha b
+__global__ void k_waxpy(double *__restrict__ y, const double *__restrict__ a, double alpha,
+                        const double *__restrict__ b, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a[i] + alpha * b[i];
+}
+
+// y = alpha x
+__global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, double alpha, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = alpha * x[i];
+}
+
+// y = 1 / x (Jacobi preconditioner from the assembled diagonal)
+__global__ void k_reciprocal(double *__restrict__ y, const double *__restrict__ x, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = x[i];
+        y[i] = d != 0.0 ? 1.0 / d : 1.0;
+    }
+}
+
+}  // namespace feod

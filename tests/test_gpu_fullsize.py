@@ -1,0 +1,85 @@
+"""Full-size parity: the 3D p=3 order-3 problem on 64^3 hexes (7,189,057 DOFs), in the launch
+configuration the benchmark times.  The oracle computes sampled entries one by one from the
+element-level definition (sum over the elements that contain the sampled DOF)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_00746_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _elements_of(dof, n, k):
+    """Elements (lexicographic) containing a global DOF of the (k n + 1)^3 lattice."""
+    m = k * n + 1
+    g = [dof % m, (dof // m) % m, dof // (m * m)]
+    cands = []
+    for d in range(3):
+        c = []
+        e = g[d] // k
+        if g[d] % k == 0 and e >= 1:
+            c.append(e - 1)
+        if e < n:
+            c.append(e)
+        cands.append(c)
+    return [ex + n * (ey + n * ez) for ez in cands[2] for ey in cands[1] for ex in cands[0]]
+
+
+def _sampled(P, u, v, dofs, n, k):
+    """Oracle values of R(u) and J(u) v at the sampled (free) DOFs."""
+    vm = v.copy()
+    vm[O.essential(P)] = 0.0
+    elems = sorted({e for g in dofs for e in _elements_of(g, n, k)})
+    re, ye, edofs = O.element_vectors(P, u, vm, elems)
+    R = {g: 0.0 for g in dofs}; Y = {g: 0.0 for g in dofs}
+    for i in range(len(elems)):
+        for l, g in enumerate(edofs[i]):
+            if g in R:
+                R[g] += re[i, l]; Y[g] += ye[i, l]
+    return np.array([R[g] for g in dofs]), np.array([Y[g] for g in dofs])
+
+
+def test_config2_sampled_parity():
+    import torch
+    from paper_2506_00746_gb300 import Operator
+    w = I.WORKLOADS["3d_p3_k3_64"]
+    V = I.lattice_vertices(3, w.n, seed=w.mesh_seed)
+    op = Operator(3, w.n, w.order, V, p=w.p)
+    assert op.n_dofs == 7_189_057
+    u = I.smooth_field(3, w.n, w.order, seed=w.state_seed)
+    v = I.uniform_vector(op.n_dofs, seed=w.dir_seed)
+    ud, vd = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
+    r = op.residual(ud).cpu().numpy()
+    op.linearize(ud)
+    y64 = op.jacobian_action(vd, precision=64).cpu().numpy()
+    v32 = vd.float()
+    y32 = op.jacobian_action(v32, precision=32).double().cpu().numpy()
+    P = O.Problem(3, w.n, w.order, V, p=w.p)
+    ess = O.essential(P)
+    rng = np.random.default_rng(7)
+    free = np.flatnonzero(~ess)
+    # random free DOFs plus the corners of tiles (DOFs shared by up to 8 elements) and a face
+    m = w.order * w.n + 1
+    tile_corner = [(6 + 6 * m + 6 * m * m), (12 + 12 * m + 12 * m * m), (96 + 96 * m + 96 * m * m)]
+    dofs = sorted(set(rng.choice(free, 48, replace=False).tolist() + tile_corner + [m * m * 5 + m * 7 + 1]))
+    R_ref, Y_ref = _sampled(P, u, v, dofs, w.n, w.order)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(r[dofs], R_ref) <= 1e-12
+    assert rel(y64[dofs], Y_ref) <= 1e-12
+    _, Y32_ref = _sampled(P, u, v32.double().cpu().numpy(), dofs, w.n, w.order)
+    assert rel(y32[dofs], Y32_ref) <= 1e-5
+    # essential rows of J v return v, of R return 0
+    eidx = np.flatnonzero(ess)[:1000]
+    np.testing.assert_array_equal(y64[eidx], v[eidx])
+    assert np.all(r[eidx] == 0.0)
+    # properties that hold at any size: symmetry of the FP64 action
+    w2 = torch.from_numpy(I.uniform_vector(op.n_dofs, seed=11)).cuda()
+    w2[torch.from_numpy(ess).cuda()] = 0.0
+    vm = vd.clone(); vm[torch.from_numpy(ess).cuda()] = 0.0
+    a = torch.dot(w2, op.jacobian_action(vm, precision=64)).item()
+    b = torch.dot(vm, op.jacobian_action(w2, precision=64)).item()
+    assert abs(a - b) <= 1e-12 * abs(a)
+    op.close()

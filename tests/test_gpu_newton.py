@@ -1,0 +1,126 @@
+"""Newton-CG on the GPU (FP64 and mixed precision), checked by the oracle: the oracle evaluates
+||R(u_gpu)|| independently, and the GPU solution matches the oracle's own Newton solution."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_00746_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(w: I.Workload):
+    import torch
+    from paper_2506_00746_gb300 import Operator
+    V = I.lattice_vertices(w.dim, w.n, seed=w.mesh_seed)
+    op = Operator(w.dim, w.n, w.order, V, p=w.p, eps=w.eps)
+    P = O.Problem(w.dim, w.n, w.order, V, p=w.p, eps=w.eps)
+    u0 = I.smooth_field(w.dim, w.n, w.order, seed=w.state_seed)
+    return op, P, u0, torch.from_numpy(u0).cuda()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_newton_2d_config(precision):
+    """2D p=3, 16x16 quads, order 2: Newton-CG to 1e-8 in FP64 and mixed precision."""
+    w = I.WORKLOADS["2d_p3_k2_16x16"]
+    op, P, u0, ud = _setup(w)
+    u = ud.clone()
+    rep = op.newton_solve(u, rtol=1e-8, inner_precision=precision)
+    assert rep["rel"] <= 1e-8
+    r0 = np.linalg.norm(O.residual(P, u0))
+    ug = u.cpu().numpy()
+    assert np.linalg.norm(O.residual(P, ug)) <= 1e-8 * r0 * 1.0001     # the oracle confirms the claim
+    u_ref, hist = O.newton(P, u0, rtol=1e-13)
+    assert np.linalg.norm(ug - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
+    op.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_newton_tight_matches_oracle(precision):
+    w = I.Workload("3d_small", 3, 4, 2)
+    op, P, u0, ud = _setup(w)
+    u = ud.clone()
+    rep = op.newton_solve(u, rtol=1e-12, cg_rtol=1e-6, inner_precision=precision)
+    assert rep["rel"] <= 1e-12
+    u_ref, _ = O.newton(P, u0, rtol=1e-13)
+    assert np.linalg.norm(u.cpu().numpy() - u_ref) <= 1e-9 * np.linalg.norm(u_ref)
+    op.close()
+
+
+def test_newton_graph_and_plain_launches_agree():
+    """Replaying CG batches as CUDA graphs gives bitwise the same iterates as plain launches."""
+    import torch
+    w = I.Workload("3d_small", 3, 3, 3)
+    op, P, u0, ud = _setup(w)
+    a, b = ud.clone(), ud.clone()
+    ra = op.newton_solve(a, inner_precision=32, use_graph=True)
+    rb = op.newton_solve(b, inner_precision=32, use_graph=False, cg_batch=5)
+    assert torch.equal(a, b)
+    assert ra["cg_hist"] == rb["cg_hist"]
+    op.close()
+
+
+def test_newton_failure_paths():
+    """Host-visible failures: iteration limits end the solve with a status, never a hang."""
+    from paper_2506_00746_gb300 import FeodError
+    w = I.Workload("3d_small", 3, 3, 2)
+    op, P, u0, ud = _setup(w)
+    u = ud.clone()
+    rep = op.newton_solve(u, max_newton=1, raise_on_error=False)
+    assert rep["status"] == "FE_ERR_NOT_CONVERGED" and rep["newton_iters"] == 1
+    u = ud.clone()
+    with pytest.raises(FeodError):
+        op.newton_solve(u, max_newton=1)
+    op.close()
+
+
+def test_cg_solve_and_adjoint_homogeneity():
+    """lambda solving J(u) lambda = F at the solution equals u/(p-1) (degree p-1 homogeneity)."""
+    import torch
+    from paper_2506_00746_gb300 import Operator
+    dim, n, k, p = 3, 4, 2, 3.0
+    V = I.lattice_vertices(dim, n, seed=0)
+    rho = I.design_field(dim, n, seed=3)
+    op = Operator(dim, n, k, V, p=p, rho=rho)
+    u = torch.from_numpy(I.smooth_field(dim, n, k, seed=1)).cuda()
+    op.newton_solve(u, rtol=1e-13, cg_rtol=1e-8)
+    op.linearize(u)
+    F = op.load_vector()
+    lam, it = op.cg_solve(F, rtol=1e-13)
+    assert it > 0
+    assert torch.linalg.norm(lam - u / (p - 1)) <= 1e-9 * torch.linalg.norm(u)
+    op.close()
+
+
+def test_compliance_gradient_against_fd():
+    """dc/drho from the autograd adjoint matches central differences on random directions."""
+    import torch
+    from paper_2506_00746_gb300 import ComplianceFn, Operator
+    dim, n, k, p = 2, 6, 2, 3.0
+    V = I.lattice_vertices(dim, n, seed=0)
+    rho0 = I.design_field(dim, n, seed=3)
+    op = Operator(dim, n, k, V, p=p, rho=rho0)
+    u0 = torch.from_numpy(I.smooth_field(dim, n, k, seed=1)).cuda()
+    kw = {"rtol": 1e-14, "cg_rtol": 1e-10}
+    rho = torch.from_numpy(rho0).cuda().requires_grad_(True)
+    c = ComplianceFn.apply(rho, op, u0, kw)
+    c.backward()
+    g = rho.grad.clone()
+    # oracle adjoint gradient at the GPU solution
+    P = O.Problem(dim, n, k, V, p=p, rho=rho0)
+    u_ref, _ = O.newton(P, u0.cpu().numpy(), rtol=1e-14)
+    lam = O.adjoint_solve(P, u_ref)
+    g_ref = -O.adjoint_grad(P, u_ref, lam)
+    assert np.linalg.norm(g.cpu().numpy() - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
+    rng = np.random.default_rng(4)
+    h = 1e-5
+    for _ in range(4):
+        d = torch.from_numpy(rng.standard_normal(n ** dim)).cuda()
+        with torch.no_grad():
+            cp = ComplianceFn.apply(rho.detach() + h * d, op, u0, kw)
+            cm = ComplianceFn.apply(rho.detach() - h * d, op, u0, kw)
+        fd = (cp - cm).item() / (2 * h)
+        assert abs(fd - torch.dot(g, d).item()) <= 1e-6 * abs(torch.dot(g, d).item())
+    op.close()
