@@ -129,16 +129,8 @@ cudaError_t dalloc(fe_ctx *c, T **p, size_t count)
 
 int64_t ipow64(int64_t b, int e) { int64_t r = 1; while (e-- > 0) r *= b; return r; }
 
-// tuned default tile edge (elements per CTA = T^dim) per (dim, order)
-int default_tile(int dim, int k)
-{
-    if (dim == 3) {
-        static const int t3[7] = { 0, 4, 3, 2, 2, 2, 2 };
-        return t3[k];
-    }
-    static const int t2[7] = { 0, 8, 8, 8, 6, 6, 6 };
-    return t2[k];
-}
+// default tile edge (elements per CTA = T^dim) per (dim, order): the largest the kernels support
+int default_tile(int dim, int k) { return max_tile(dim, k); }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -316,6 +308,7 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
 
     // tile size
     int T = (opts && opts->tile > 0) ? opts->tile : default_tile(dim, k);
+    if (T > max_tile(dim, k)) T = max_tile(dim, k);
     if (T > n) T = n;
     const int team = dim == 3 ? c->d1 * c->d1 : c->d1;
     for (;;) {

@@ -537,7 +537,7 @@ __host__ __device__ inline size_t smem_bytes(int S, int T, size_t tc, int n_inpu
 
 // Partially assembled Jacobian action: y = P^T G^T B^T (T_q . B G P v).
 template <int DIM, int D1, typename TC, typename TIO>
-__global__ void k_jv_pa(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
+__global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_jv_pa(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
                         const TC *__restrict__ Tq, const TIO *__restrict__ v, TIO *__restrict__ y,
                         TC *__restrict__ halo)
 {
@@ -602,7 +602,7 @@ __device__ __forceinline__ void load_geo(const double *__restrict__ ge, int NQ, 
 // is the derivative part of the flux evaluated on dual numbers seeded with the unit directions of
 // the reference gradient (forward-mode AD at the quadrature point, Eq. 2).
 template <int DIM, int D1>
-__global__ void k_residual(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<double> Bs,
+__global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_residual(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<double> Bs,
                            const double *__restrict__ u, double *__restrict__ r, double *__restrict__ halo,
                            double *__restrict__ T64, float *__restrict__ T32, int want_r)
 {
@@ -682,7 +682,7 @@ __global__ void k_residual(const __grid_constant__ OpParams P, const __grid_cons
 
 // Stateless Jacobian action J(u) v: one dual direction seeded with the reference gradient of v.
 template <int DIM, int D1, typename TC, typename TIO>
-__global__ void k_jv_dual(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
+__global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_jv_dual(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
                           const double *__restrict__ u, const TIO *__restrict__ v, TIO *__restrict__ y,
                           TC *__restrict__ halo)
 {
@@ -738,7 +738,7 @@ __global__ void k_jv_dual(const __grid_constant__ OpParams P, const __grid_const
 // Jacobi diagonal diag(J)_l = sum_q sum_ab T_ab(q) dphi_l/dxi_a dphi_l/dxi_b, sum-factorised with
 // the squared / product 1D tables.
 template <int DIM, int D1, typename TC>
-__global__ void k_diag(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
+__global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_diag(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs,
                        const TC *__restrict__ Tq, double *__restrict__ dg, TC *__restrict__ halo)
 {
     using SH = Shape<DIM, D1>;
@@ -857,7 +857,7 @@ __global__ void k_diag(const __grid_constant__ OpParams P, const __grid_constant
 // Adjoint design gradient: grad[e] = lambda_e^T dr_e/drho_e, with d/drho taken by a dual number
 // seeded on kappa_rho (derivative kappa_rho'(rho_e)) at each quadrature point; element-local sum.
 template <int DIM, int D1>
-__global__ void k_vjp(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<double> Bs,
+__global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_vjp(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<double> Bs,
                       const double *__restrict__ u, const double *__restrict__ lam, double *__restrict__ grad)
 {
     using SH = Shape<DIM, D1>;
@@ -1020,7 +1020,15 @@ struct Ops {
         const size_t s2d = smem_bytes<DIM, D1>(c->S, c->T, sizeof(double), 2);
         const size_t s2f = smem_bytes<DIM, D1>(c->S, c->T, sizeof(float), 2);
         cudaError_t e = cudaSuccess, e2;
-#define FEOD_RAISE(k, b) if ((e2 = raise_smem(k, b)) != cudaSuccess) e = e2
+        const int threads = nthreads(c);
+        // raise the shared-memory limit and check that the block fits the kernel's registers
+#define FEOD_RAISE(k, b)                                                                          \
+    do {                                                                                          \
+        if ((e2 = raise_smem(k, b)) != cudaSuccess) e = e2;                                       \
+        cudaFuncAttributes fa;                                                                    \
+        if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.maxThreadsPerBlock < threads)      \
+            e = cudaErrorLaunchOutOfResources;                                                    \
+    } while (0)
         FEOD_RAISE((k_residual<DIM, D1>), s1d);
         FEOD_RAISE((k_jv_pa<DIM, D1, double, double>), s1d);
         FEOD_RAISE((k_jv_pa<DIM, D1, float, float>), s1f);

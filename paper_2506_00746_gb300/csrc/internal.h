@@ -15,6 +15,19 @@ namespace feod {
 constexpr int MAXQ = 7;                 // points per direction: order 6 -> 7 nodes / Gauss points
 constexpr int MAX_ORDER = 6;
 
+// Largest tile edge (elements per CTA = tile^dim) per (dim, order); also the default.  The
+// element kernels are compiled with launch bounds for this many elements per CTA, so a context
+// may use this tile or a smaller one.
+constexpr int max_tile(int dim, int order)
+{
+    return dim == 3 ? (order == 1 ? 4 : order == 2 ? 3 : 2) : (order <= 3 ? 8 : 6);
+}
+constexpr int max_threads(int dim, int order)
+{
+    return dim == 3 ? max_tile(3, order) * max_tile(3, order) * max_tile(3, order) * (order + 1) * (order + 1)
+                    : max_tile(2, order) * max_tile(2, order) * (order + 1);
+}
+
 // Slot code of a tile slot: bits 0..29 global DOF, bit 30 essential, bit 31 halo (the slot's DOF
 // is owned by a neighbouring tile; this tile's partial sum goes to the halo buffer).
 constexpr uint32_t SLOT_GMASK = 0x3FFFFFFFu;
