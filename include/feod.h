@@ -127,6 +127,31 @@ fe_status fe_jacobian_action(fe_ctx *ctx, const double *u, const void *v, void *
 fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host, int precision,
                                   void *stream);
 
+/* fe_jacobian_action_noalloc: the same y = J v as fe_jacobian_action with u == NULL (cached
+ * linearisation, precision 64 / 32 / -32 with the same meaning), for callers that must not
+ * allocate device memory while they run -- e.g. code executing while a stream capture in global
+ * mode is active (cudaMalloc is not permitted there), or an application whose GPU memory is all
+ * handed out by its own pool allocator, so that a cudaMalloc would fail or disturb the pool.
+ * The paper has no counterpart; it is a deployment variant of the Jacobian action.
+ *
+ * Scratch: the cross-tile partial sums that fe_jacobian_action keeps in the context's halo buffer
+ * go instead to one file-scope device array of FE_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU
+ * that loads the library holds until the process exits.  A problem needs
+ * ntiles * (order*tile + 1)^dim * w bytes of it (w = 8 for precision 64, else 4; 3D order 3 with
+ * the default tile fits up to 46^3 elements in FP32); larger problems return FE_ERR_UNSUPPORTED
+ * with a message and launch nothing.  Every scratch entry that is read is written earlier in the
+ * same call, so nothing needs clearing between calls.
+ *
+ * The first call on a device resolves the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other contexts on the same device) race
+ * and produce wrong results -- serialise them.  The call itself allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  v, y: device arrays as for fe_jacobian_action;
+ * FE_ERR_STATE without a cached linearisation, FE_ERR_ARG if the current device is not the
+ * context's. */
+#define FE_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+fe_status fe_jacobian_action_noalloc(fe_ctx *ctx, const void *v, void *y, int precision, void *stream);
+
 /* fe_jacobian_diagonal: diag(J) of the cached linearisation (1 on essential DOFs), FP64. */
 fe_status fe_jacobian_diagonal(fe_ctx *ctx, double *diag, void *stream);
 

@@ -69,6 +69,7 @@ _SIGS = {
     "fe_linearize": (c_int, [_CTX, c_void_p, c_void_p]),
     "fe_jacobian_action": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "fe_jacobian_action_host": (c_int, [_CTX, c_void_p, c_void_p, c_int, c_void_p]),
+    "fe_jacobian_action_noalloc": (c_int, [_CTX, c_void_p, c_void_p, c_int, c_void_p]),
     "fe_jacobian_diagonal": (c_int, [_CTX, c_void_p, c_void_p]),
     "fe_load_vector": (c_int, [_CTX, c_void_p, c_void_p]),
     "fe_node_coords": (c_int, [_CTX, c_void_p, c_void_p]),
@@ -172,6 +173,12 @@ def fe_jacobian_action(ctx, u, v, y, precision: int, stream=None):
 def fe_jacobian_action_host(ctx, v_host, y_host, precision: int, stream=None):
     check(library().fe_jacobian_action_host(ctx, ptr(v_host), ptr(y_host), precision, stream_handle(stream)),
           "fe_jacobian_action_host", ctx)
+
+
+def fe_jacobian_action_noalloc(ctx, v, y, precision: int, stream=None):
+    """Allocation-free variant of the cached Jacobian action (static device scratch; see feod.h)."""
+    check(library().fe_jacobian_action_noalloc(ctx, ptr(v), ptr(y), precision, stream_handle(stream)),
+          "fe_jacobian_action_noalloc", ctx)
 
 
 def fe_jacobian_diagonal(ctx, diag, stream=None):

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -859,4 +860,62 @@ extern "C" fe_status fe_launch_count(const fe_ctx *c, int64_t *launches)
     if (!c || !launches) return FE_ERR_ARG;
     *launches = c->launches;
     return FE_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Jacobian action without allocation: scratch in a file-scope device array
+// ------------------------------------------------------------------------------------------------
+// Holds the cross-tile partial sums (the role of the context's halo buffer) for
+// fe_jacobian_action_noalloc.  Every GPU that loads the library keeps it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+
+// Once per device, with that device current: the device address of the scratch array.  In host
+// code the array's name is only a host-side stand-in, so kernels must be given this address.
+fe_status noalloc_scratch_address(fe_ctx *c, int dev, void **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(c, FE_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                        cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return FE_OK;
+}
+}  // namespace
+
+extern "C" fe_status fe_jacobian_action_noalloc(fe_ctx *c, const void *v, void *y, int precision, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!v || !y || v == y) return fail(c, FE_ERR_ARG, "fe_jacobian_action_noalloc: null or aliased vectors");
+    if (precision != 64 && precision != 32 && precision != -32)
+        return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
+    const size_t word = precision == 64 ? sizeof(double) : sizeof(float);
+    const size_t need = (size_t)c->ntiles * (size_t)c->S * word;
+    if (need > (size_t)FE_NOALLOC_SCRATCH_BYTES)
+        return fail(c, FE_ERR_UNSUPPORTED,
+                    "fe_jacobian_action_noalloc: problem needs %zu bytes of scratch, the static array holds %u",
+                    need, (unsigned)FE_NOALLOC_SCRATCH_BYTES);
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != c->device || dev < 0 || dev >= kMaxDevices)
+        return fail(c, FE_ERR_ARG, "fe_jacobian_action_noalloc: current device %d is not the context's (%d)", dev,
+                    c->device);
+    void *scratch = nullptr;
+    fe_status s = noalloc_scratch_address(c, dev, &scratch);
+    if (s != FE_OK) return s;
+    // run the regular launchers with the static array standing in for the context's halo buffer
+    void *own = c->d_halo;
+    c->d_halo = scratch;
+    s = apply_jv_cached(c, v, y, precision, as_stream(stream));
+    c->d_halo = own;
+    return s;
 }
