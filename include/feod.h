@@ -79,6 +79,9 @@ typedef struct {
 typedef struct {
     int tile;                  /* elements per tile edge: one CTA owns tile^dim elements;
                                   0 = tuned default                                           */
+    int no_pipeline;           /* 1: apply the cached Jacobian with the per-element kernel
+                                  (element-by-element sum factorisation, staged in-tile G^T)
+                                  instead of the tile-level one (3D); for comparison only     */
 } fe_setup_opts;
 
 /* fe_setup: build a context for the mesh, order k (1..6) and quadrature q1d (0 or k+1 Gauss
@@ -137,7 +140,8 @@ fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host,
  * Scratch: the cross-tile partial sums that fe_jacobian_action keeps in the context's halo buffer
  * go instead to one file-scope device array of FE_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU
  * that loads the library holds until the process exits.  A problem needs
- * ntiles * (order*tile + 1)^dim * w bytes of it (w = 8 for precision 64, else 4; 3D order 3 with
+ * ntiles * S * w bytes of it (S = (order*tile + 1)^dim rounded up to a multiple of 4; w = 8 for
+ * precision 64, else 4; 3D order 3 with
  * the default tile fits up to 46^3 elements in FP32); larger problems return FE_ERR_UNSUPPORTED
  * with a message and launch nothing.  Every scratch entry that is read is written earlier in the
  * same call, so nothing needs clearing between calls.

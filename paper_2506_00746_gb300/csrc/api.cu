@@ -162,9 +162,10 @@ fe_status ensure_work(fe_ctx *c)
 
 fe_status ensure_tangent(fe_ctx *c, bool f64, bool f32)
 {
-    const size_t n = (size_t)c->nepad * c->NS * c->NQ;
-    if (f64 && !c->d_T64) { CK(dalloc(c, &c->d_T64, n)); CK(cudaMemset(c->d_T64, 0, n * sizeof(double))); }
-    if (f32 && !c->d_T32) { CK(dalloc(c, &c->d_T32, n)); CK(cudaMemset(c->d_T32, 0, n * sizeof(float))); }
+    // zero-filled: padded elements of ragged tiles keep a zero tangent, so they add exact zeros
+    const size_t n64 = (size_t)c->ntiles * c->tqs64, n32 = (size_t)c->ntiles * c->tqs32;
+    if (f64 && !c->d_T64) { CK(dalloc(c, &c->d_T64, n64)); CK(cudaMemset(c->d_T64, 0, n64 * sizeof(double))); }
+    if (f32 && !c->d_T32) { CK(dalloc(c, &c->d_T32, n32)); CK(cudaMemset(c->d_T32, 0, n32 * sizeof(float))); }
     if (!c->d_diag) CK(dalloc(c, &c->d_diag, (size_t)c->nl));
     return FE_OK;
 }
@@ -303,6 +304,8 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
     int smem_optin = 0;
     CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    c->smem_optin = smem_optin;
+    c->no_pipeline = opts && opts->no_pipeline;
 
     c->ops = find_ops(dim, c->d1);
     if (!c->ops) return fail(c, FE_ERR_UNSUPPORTED, "no kernels built for dim %d order %d", dim, k);
@@ -326,11 +329,45 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     c->nepad = c->ntiles * c->NE;
     c->SE = k * T + 1;
     c->S = (int)ipow64(c->SE, dim);
-    if ((double)c->ntiles * c->S >= 4294967295.0)
+    c->Spad = (c->S + 3) & ~3;
+    const int64_t tq_block = (int64_t)c->NE * c->NS * c->NQ;
+    c->tqs32 = (tq_block + 3) & ~(int64_t)3;
+    c->tqs64 = (tq_block + 1) & ~(int64_t)1;
+    if ((double)c->ntiles * c->Spad >= 4294967295.0)
         return fail(c, FE_ERR_UNSUPPORTED, "tile slot index exceeds 32 bits");
 
+    // --- in-tile G^T table: for every slot, the staged element outputs (el*NQ + local node) that
+    //     sum into it, in ascending (z, y, x) element order; identical for every tile ---
+    std::vector<uint16_t> gt_off(c->S + 1), gt_src;
+    {
+        gt_src.reserve((size_t)c->NE * c->NQ);
+        for (int s = 0; s < c->S; ++s) {
+            gt_off[s] = (uint16_t)gt_src.size();
+            const int sc[3] = { s % c->SE, (s / c->SE) % c->SE, dim == 3 ? s / (c->SE * c->SE) : 0 };
+            int ce[3][2], cl[3][2], cn[3];
+            for (int d = 0; d < 3; ++d) {
+                cn[d] = 0;
+                if (d >= dim) { ce[d][0] = 0; cl[d][0] = 0; cn[d] = 1; continue; }
+                for (int te = 0; te < T; ++te) {
+                    const int a = sc[d] - k * te;
+                    if (a >= 0 && a <= k) { ce[d][cn[d]] = te; cl[d][cn[d]] = a; cn[d]++; }
+                }
+            }
+            for (int iz = 0; iz < cn[2]; ++iz)
+                for (int iy = 0; iy < cn[1]; ++iy)
+                    for (int ix = 0; ix < cn[0]; ++ix) {
+                        const int el = ce[0][ix] + T * (ce[1][iy] + T * ce[2][iz]);
+                        const int lo = cl[0][ix] + c->d1 * (cl[1][iy] + c->d1 * cl[2][iz]);
+                        gt_src.push_back((uint16_t)(el * c->NQ + lo));
+                    }
+        }
+        gt_off[c->S] = (uint16_t)gt_src.size();
+        if (gt_src.size() != (size_t)c->NE * c->NQ || (size_t)c->NE * c->NQ > 65535)
+            return fail(c, FE_ERR_UNSUPPORTED, "in-tile G^T table does not fit 16-bit indices");
+    }
+
     // --- G as explicit index arrays: slot codes per tile, and the transposed halo index ---
-    std::vector<uint32_t> slot((size_t)c->ntiles * c->S);
+    std::vector<uint32_t> slot((size_t)c->ntiles * c->Spad, SLOT_INVALID);
     std::vector<uint64_t> halo_pairs;   // (g << 32) | (t*S + s)
     for (int64_t t = 0; t < c->ntiles; ++t) {
         int64_t tc[3] = { 0, 0, 0 }, r = t;
@@ -349,9 +386,9 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
             if (valid) {
                 const int64_t g = gl[0] + m * (gl[1] + (dim == 3 ? m * gl[2] : 0));
                 code = (uint32_t)g | (ess ? SLOT_ESS : 0u) | (halo ? SLOT_HALO : 0u);
-                if (halo && !ess) halo_pairs.push_back(((uint64_t)g << 32) | (uint64_t)(t * c->S + s));
+                if (halo && !ess) halo_pairs.push_back(((uint64_t)g << 32) | (uint64_t)(t * c->Spad + s));
             }
-            slot[(size_t)t * c->S + s] = code;
+            slot[(size_t)t * c->Spad + s] = code;
         }
     }
     std::sort(halo_pairs.begin(), halo_pairs.end());
@@ -387,6 +424,10 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
 
     // --- device data ---
     const int64_t nvert = ipow64(n + 1, dim);
+    CK(dalloc(c, &c->d_gt_off, gt_off.size()));
+    CK(dalloc(c, &c->d_gt_src, gt_src.size()));
+    CK(cudaMemcpy(c->d_gt_off, gt_off.data(), gt_off.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_gt_src, gt_src.data(), gt_src.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_slot, slot.size()));
     CK(cudaMemcpy(c->d_slot, slot.data(), slot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_fix_g, fix_g.size()));
@@ -402,7 +443,7 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     CK(dalloc(c, &c->d_geo, (size_t)c->nepad * c->NG * c->NQ));
     {
         double *h = nullptr;
-        CK(dalloc(c, &h, (size_t)c->ntiles * c->S));
+        CK(dalloc(c, &h, (size_t)c->ntiles * c->Spad));
         c->d_halo = h;
     }
     CK(dalloc(c, &c->d_err, 1));
@@ -432,6 +473,8 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     // --- kernel parameter blocks ---
     c->op.n = n; c->op.T = T; c->op.nt = c->nt; c->op.S = c->S; c->op.SE = c->SE; c->op.law = c->law;
     c->op.ntiles = c->ntiles; c->op.slot = c->d_slot; c->op.geo = c->d_geo;
+    c->op.Spad = c->Spad; c->op.tqs32 = c->tqs32; c->op.tqs64 = c->tqs64;
+    c->op.gt_off = c->d_gt_off; c->op.gt_src = c->d_gt_src; c->op.err = c->d_err;
     c->op.kr = c->d_kr; c->op.dkr = c->d_dkr; c->op.skip = nullptr;
     c->op.law_a = 0.5 * (prob->p - 2.0); c->op.eps2 = prob->eps * prob->eps;
     c->fix.nfix = c->nfix; c->fix.fix_g = c->d_fix_g; c->fix.fix_off = c->d_fix_off; c->fix.fix_h = c->d_fix_h;
@@ -475,7 +518,7 @@ extern "C" fe_status fe_setup_ex(const fe_mesh *mesh, int order, int q1d, const 
 extern "C" void fe_destroy(fe_ctx *c)
 {
     if (!c) return;
-    void *ptrs[] = { c->d_slot, c->d_fix_g, c->d_fix_off, c->d_fix_h, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
+    void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_fix_off, c->d_fix_h, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
                      c->d_dkr, c->d_T64, c->d_T32, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
                      c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_state, c->w_partial };
     for (void *p : ptrs)
@@ -899,7 +942,7 @@ extern "C" fe_status fe_jacobian_action_noalloc(fe_ctx *c, const void *v, void *
     if (precision != 64 && precision != 32 && precision != -32)
         return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
     const size_t word = precision == 64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)c->ntiles * (size_t)c->S * word;
+    const size_t need = (size_t)c->ntiles * (size_t)c->Spad * word;
     if (need > (size_t)FE_NOALLOC_SCRATCH_BYTES)
         return fail(c, FE_ERR_UNSUPPORTED,
                     "fe_jacobian_action_noalloc: problem needs %zu bytes of scratch, the static array holds %u",

@@ -155,6 +155,24 @@ __device__ __forceinline__ int qidx(int lane, int i)
     return DIM == 3 ? i + D1 * lane : lane + D1 * i;
 }
 
+// per-tile stride of the stored tangent of compute type TC
+template <typename TC>
+__device__ __forceinline__ int64_t tq_stride(const OpParams &P)
+{
+    return sizeof(TC) == 8 ? P.tqs64 : P.tqs32;
+}
+
+// The stored tangent of a tile is [component][tile quadrature point], the tile's points numbered
+// lexicographically over the (k+1)T per direction lattice of the tile (x fastest); one component
+// block holds T^dim (k+1)^dim values.  Index of point q of the tile-local element at ec:
+template <int DIM, int D1>
+__device__ __forceinline__ int tile_qp(const int (&ec)[3], int q, int T)
+{
+    const int QT = D1 * T;
+    const int qx = q % D1, qy = (q / D1) % D1, qz = DIM == 3 ? q / (D1 * D1) : 0;
+    return (ec[0] * D1 + qx) + QT * ((ec[1] * D1 + qy) + (DIM == 3 ? QT * (ec[2] * D1 + qz) : 0));
+}
+
 struct TileInfo {
     int T1[3];    // tile coordinates
     int nv[3];    // valid elements of the tile per direction (ragged last tile)
@@ -205,7 +223,7 @@ __device__ __forceinline__ int64_t elem_public(const OpParams &P, const TileInfo
 template <typename TC, typename TIN, bool MASK_ESSENTIAL>
 __device__ __forceinline__ void load_slots(const OpParams &P, int64_t t, const TIN *__restrict__ v, TC *Vs)
 {
-    const uint32_t *sl = P.slot + t * P.S;
+    const uint32_t *sl = P.slot + t * P.Spad;
     for (int s = threadIdx.x; s < P.S; s += blockDim.x) {
         uint32_t c = sl[s];
         TC val = TC(0);
@@ -262,7 +280,7 @@ __device__ __forceinline__ void scatter_tile(const OpParams &P, int64_t t, const
     constexpr int K = D1 - 1;
     constexpr int NQ = Shape<DIM, D1>::NQ;
     const int SE = P.SE, T = P.T;
-    const uint32_t *sl = P.slot + t * P.S;
+    const uint32_t *sl = P.slot + t * P.Spad;
     for (int s = threadIdx.x; s < P.S; s += blockDim.x) {
         const uint32_t code = sl[s];
         if (code == SLOT_INVALID) continue;
@@ -287,7 +305,7 @@ __device__ __forceinline__ void scatter_tile(const OpParams &P, int64_t t, const
                 }
         const uint32_t g = code & SLOT_GMASK;
         if (code & SLOT_HALO) {
-            if (!(code & SLOT_ESS)) halo[t * P.S + s] = acc;
+            if (!(code & SLOT_ESS)) halo[t * P.Spad + s] = acc;
         } else if (code & SLOT_ESS) {
             if (OUT == OUT_JV) y[g] = vorig[g];
             else if (OUT == OUT_RES) y[g] = TIO(0);
@@ -561,19 +579,20 @@ __global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_jv_pa(const __grid
     gather_line<DIM, D1, TC>(P, Vs, ec, lane, u);
     TC g[DIM][D1];
     fwd<DIM, D1, TC>(u, b0, b1, Bs, lane, g);
-    const TC *Te = Tq + (t * NE + el) * (int64_t)(SH::NS * SH::NQ);
+    const TC *Tt = Tq + t * tq_stride<TC>(P);
+    const int CS = NE * SH::NQ;
     TC f[DIM][D1], s[D1];
 #pragma unroll
     for (int i = 0; i < D1; ++i) {
-        const int q = qidx<DIM, D1>(lane, i);
+        const TC *Te = Tt + tile_qp<DIM, D1>(ec, qidx<DIM, D1>(lane, i), T);
         if constexpr (DIM == 3) {
-            const TC txx = Te[q], tyy = Te[SH::NQ + q], tzz = Te[2 * SH::NQ + q];
-            const TC txy = Te[3 * SH::NQ + q], txz = Te[4 * SH::NQ + q], tyz = Te[5 * SH::NQ + q];
+            const TC txx = Te[0], tyy = Te[CS], tzz = Te[2 * CS];
+            const TC txy = Te[3 * CS], txz = Te[4 * CS], tyz = Te[5 * CS];
             f[0][i] = txx * g[0][i] + txy * g[1][i] + txz * g[2][i];
             f[1][i] = txy * g[0][i] + tyy * g[1][i] + tyz * g[2][i];
             f[2][i] = txz * g[0][i] + tyz * g[1][i] + tzz * g[2][i];
         } else {
-            const TC txx = Te[q], tyy = Te[SH::NQ + q], txy = Te[2 * SH::NQ + q];
+            const TC txx = Te[0], tyy = Te[CS], txy = Te[2 * CS];
             f[0][i] = txx * g[0][i] + txy * g[1][i];
             f[1][i] = txy * g[0][i] + tyy * g[1][i];
         }
@@ -654,11 +673,11 @@ __global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_residual(const __g
             } else {
                 tv[0] = qd[0].d[0]; tv[1] = qd[1].d[1]; tv[2] = qd[0].d[1];
             }
-            const int64_t tb = eint * (int64_t)(SH::NS * SH::NQ) + q;
+            const int tl = tile_qp<DIM, D1>(ec, q, T), CS = NE * SH::NQ;
 #pragma unroll
             for (int c = 0; c < SH::NS; ++c) {
-                if (T64) T64[tb + c * SH::NQ] = tv[c];
-                if (T32) T32[tb + c * SH::NQ] = (float)tv[c];
+                if (T64) T64[t * P.tqs64 + tl + c * CS] = tv[c];
+                if (T32) T32[t * P.tqs32 + tl + c * CS] = (float)tv[c];
             }
 #pragma unroll
             for (int d = 0; d < DIM; ++d) f[d][i] = qd[d].v;
@@ -752,16 +771,19 @@ __global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_diag(const __grid_
     const TileInfo tinf = tile_info<DIM>(P, t);
     const int el = threadIdx.x / SH::TEAM, lane = threadIdx.x % SH::TEAM;
     TC *b0 = bufs + el * 6 * NQ;
-    const TC *Te = Tq + (t * NE + el) * (int64_t)(SH::NS * NQ);
+    const TC *Tt = Tq + t * tq_stride<TC>(P);
+    const int CS = NE * NQ;
+    int ec[3];
+    elem_coords<DIM>(el, T, ec);
     TC yl[D1];
     if constexpr (DIM == 3) {
         const int ti = lane % D1, tj = lane / D1;
         TC tq[6][D1];
 #pragma unroll
         for (int i = 0; i < D1; ++i) {
-            const int q = qidx<DIM, D1>(lane, i);
+            const int q = tile_qp<DIM, D1>(ec, qidx<DIM, D1>(lane, i), T);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) tq[c][i] = Te[c * NQ + q];
+            for (int c = 0; c < 6; ++c) tq[c][i] = Tt[c * CS + q];
         }
         // x: (qy,qz) = (ti,tj) -> six arrays [qz][qy][a]
 #pragma unroll
@@ -821,9 +843,9 @@ __global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_diag(const __grid_
         TC tq[3][D1];
 #pragma unroll
         for (int i = 0; i < D1; ++i) {
-            const int q = qidx<DIM, D1>(lane, i);
+            const int q = tile_qp<DIM, D1>(ec, qidx<DIM, D1>(lane, i), T);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) tq[c][i] = Te[c * NQ + q];
+            for (int c = 0; c < 3; ++c) tq[c][i] = Tt[c * CS + q];
         }
         // y: thread qx = lane -> [b][qx]
 #pragma unroll
@@ -916,6 +938,13 @@ __global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_vjp(const __grid_c
 // --------------------------------------------------------------------------------------------
 // Host launchers of one (dim, order) instantiation
 // --------------------------------------------------------------------------------------------
+}  // namespace feod
+
+#include "tma.cuh"
+#include "jv_tile.cuh"
+
+namespace feod {
+
 template <typename K>
 inline cudaError_t raise_smem(K kernel, size_t bytes)
 {
@@ -957,12 +986,52 @@ struct Ops {
         const BasisT<TC> *bs;
         if constexpr (sizeof(TC) == 8) { Tq = reinterpret_cast<const TC *>(c->d_T64); bs = reinterpret_cast<const BasisT<TC> *>(&c->b64); }
         else { Tq = reinterpret_cast<const TC *>(c->d_T32); bs = reinterpret_cast<const BasisT<TC> *>(&c->b32); }
+        const char *name = sizeof(TC) == 8 ? "jv_pa_f64" : "jv_pa_f32";
+        if constexpr (DIM == 3) {
+            if (c->pipe_grid[variant<TC, TIO>()] > 0) {
+                constexpr int TT = max_tile(3, D1 - 1);
+                const size_t tsm = tile_smem_bytes<D1, TT, TC>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32);
+                {
+                    LaunchScope ls(c, name, st);
+                    k_jv_tile<D1, TT, TC, TIO><<<(unsigned)c->ntiles, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                        c->op, *bs, Tq, v, y, reinterpret_cast<TC *>(c->d_halo));
+                }
+                fixup<TC, TIO>(c, y, st);
+                return;
+            }
+        }
         {
-            LaunchScope ls(c, sizeof(TC) == 8 ? "jv_pa_f64" : "jv_pa_f32", st);
+            LaunchScope ls(c, name, st);
             k_jv_pa<DIM, D1, TC, TIO><<<(unsigned)c->ntiles, nthreads(c), sm, st>>>(
                 c->op, *bs, Tq, v, y, reinterpret_cast<TC *>(c->d_halo));
         }
         fixup<TC, TIO>(c, y, st);
+    }
+
+    // index of the (compute, I/O) variant in fe_ctx::pipe_grid
+    template <typename TC, typename TIO>
+    static constexpr int variant() { return sizeof(TC) == 8 ? 0 : (sizeof(TIO) == 4 ? 1 : 2); }
+
+    // Enable the tile-level kernel of one variant when the context uses the compiled tile edge and
+    // its shared memory and registers fit; otherwise the per-element kernel applies J.
+    template <typename TC, typename TIO>
+    static cudaError_t prepare_tile(fe_ctx *c)
+    {
+        c->pipe_grid[variant<TC, TIO>()] = 0;
+        if constexpr (DIM == 3) {
+            constexpr int TT = max_tile(3, D1 - 1);
+            if (c->no_pipeline || c->T != TT) return cudaSuccess;
+            const size_t tsm = tile_smem_bytes<D1, TT, TC>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32);
+            if (tsm > (size_t)c->smem_optin) return cudaSuccess;
+            cudaError_t e = raise_smem(k_jv_tile<D1, TT, TC, TIO>, tsm);
+            if (e != cudaSuccess) return e;
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, k_jv_tile<D1, TT, TC, TIO>);
+            if (e != cudaSuccess) return e;
+            if (fa.maxThreadsPerBlock < TileShape<D1, TT>::THREADS) return cudaSuccess;
+            c->pipe_grid[variant<TC, TIO>()] = 1;
+        }
+        return cudaSuccess;
     }
     static void jv_pa_64(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<double, double>(c, v, y, st); }
     static void jv_pa_32(fe_ctx *c, const float *v, float *y, cudaStream_t st) { jv_pa<float, float>(c, v, y, st); }
@@ -1040,7 +1109,10 @@ struct Ops {
         FEOD_RAISE((k_diag<DIM, D1, float>), s1f);
         FEOD_RAISE((k_vjp<DIM, D1>), s2d);
 #undef FEOD_RAISE
-        return e;
+        if (e != cudaSuccess) return e;
+        if ((e = prepare_tile<double, double>(c)) != cudaSuccess) return e;
+        if ((e = prepare_tile<float, float>(c)) != cudaSuccess) return e;
+        return prepare_tile<float, double>(c);
     }
 
     static const OpTable *table()

@@ -57,9 +57,15 @@ struct OpParams {
     int nt;           // tiles per direction
     int S;            // slots per tile = (k T + 1)^dim
     int SE;           // slots per tile edge = k T + 1
+    int Spad;         // per-tile stride of slot codes and halo entries (S rounded up to 4)
     int law;          // LawKind
     int64_t ntiles;
-    const uint32_t *slot;   // [ntiles][S]
+    int64_t tqs32;    // per-tile stride (floats) of the FP32 tangent, a multiple of 4
+    int64_t tqs64;    // per-tile stride (doubles) of the FP64 tangent, a multiple of 2
+    const uint32_t *slot;   // [ntiles][Spad]
+    const uint16_t *gt_off; // in-tile G^T table: slot s sums Ye[gt_src[j]], j in [gt_off[s], gt_off[s+1])
+    const uint16_t *gt_src; // (same for every tile; padded elements contribute exact zeros)
+    int *err;               // device error word (bounded waits that time out set it)
     const double *geo;      // [nepad][NG][NQ]
     const double *kr;       // [nepad] kappa_rho per element (internal order) or nullptr
     const double *dkr;      // [nepad] kappa_rho' per element or nullptr
@@ -122,6 +128,15 @@ const OpTable *find_ops(int dim, int d1);
 struct fe_ctx {
     int dim = 0, n = 0, k = 0, d1 = 0, q1 = 0;
     int T = 0, nt = 0, S = 0, SE = 0, NE = 0;   // tiling
+    int Spad = 0;                               // per-tile slot stride
+    int64_t tqs32 = 0, tqs64 = 0;               // per-tile tangent strides (elements)
+    uint16_t *d_gt_off = nullptr, *d_gt_src = nullptr;   // in-tile G^T table
+    // persistent grid of the pipelined 3D J v kernels per variant [FP64, FP32, FP32 with FP64
+    // vectors]; 0 = use the one-CTA-per-tile kernel
+    int pipe_grid[3] = { 0, 0, 0 };
+    bool no_pipeline = false;
+    int smem_optin = 0;
+    int *h_err = nullptr;                       // pinned mirror of d_err
     int NQ = 0, NS = 0, NG = 0;                 // points per element, sym entries, geo comps
     int64_t nl = 0, nfree = 0, ne = 0, nepad = 0, ntiles = 0;
     int device = 0;

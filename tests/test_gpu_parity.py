@@ -106,6 +106,35 @@ def test_tile_shapes_agree(tile):
     op.close()
 
 
+@pytest.mark.parametrize("n,k", [(7, 1), (5, 2), (6, 3), (3, 3), (4, 4), (3, 5), (2, 6)])
+def test_pipelined_and_simple_jacobian_kernels(n, k):
+    """The persistent TMA-pipelined J v and the one-CTA-per-tile J v both match the oracle."""
+    import torch
+    from paper_2506_00746_gb300 import Operator
+    V = I.lattice_vertices(3, n, seed=0)
+    P = O.Problem(3, n, k, V, p=3.0)
+    u = I.smooth_field(3, n, k, seed=1)
+    v = I.uniform_vector(P.n_dofs, seed=2)
+    ud, vd = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
+    y_ref = O.jv(P, u, v)
+    v32 = vd.float()
+    y_ref32 = O.jv(P, u, v32.double().cpu().numpy())
+    outs = []
+    for pipeline in (True, False):
+        op = Operator(3, n, k, V, p=3.0, pipeline=pipeline)
+        op.linearize(ud)
+        y64 = op.jacobian_action(vd, precision=64).cpu().numpy()
+        y32 = op.jacobian_action(v32, precision=32).double().cpu().numpy()
+        y32d = op.jacobian_action(v32.double(), precision=-32).cpu().numpy()
+        assert _rel(y64, y_ref) <= TOL64
+        assert _rel(y32, y_ref32) <= TOL32
+        np.testing.assert_array_equal(y32d, y32)
+        outs.append((y64, y32))
+        op.close()
+    assert _rel(outs[0][0], outs[1][0]) <= 1e-14
+    assert _rel(outs[0][1], outs[1][1]) <= 1e-6
+
+
 def test_bitwise_reproducible():
     import torch
     op, P, u, v, ud, vd = _case(3, 6, 3)
