@@ -139,11 +139,10 @@ fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host,
  *
  * Scratch: the cross-tile partial sums that fe_jacobian_action keeps in the context's halo buffer
  * go instead to one file-scope device array of FE_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU
- * that loads the library holds until the process exits.  A problem needs
- * ntiles * S * w bytes of it (S = (order*tile + 1)^dim rounded up to a multiple of 4; w = 8 for
- * precision 64, else 4; 3D order 3 with
- * the default tile fits up to 46^3 elements in FP32); larger problems return FE_ERR_UNSUPPORTED
- * with a message and launch nothing.  Every scratch entry that is read is written earlier in the
+ * that loads the library holds until the process exits.  A problem needs one word (8 bytes for
+ * precision 64, else 4) per cross-tile partial sum -- about 127 per tile for 3D order 3 with the
+ * default 2^3-element tile, so up to about 64^3 elements in FP32 and 50^3 in FP64; larger
+ * problems return FE_ERR_UNSUPPORTED with a message and launch nothing.  Every scratch entry that is read is written earlier in the
  * same call, so nothing needs clearing between calls.
  *
  * The first call on a device resolves the array's device address (cudaGetSymbolAddress, with

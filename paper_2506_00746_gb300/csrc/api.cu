@@ -391,17 +391,19 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
             slot[(size_t)t * c->Spad + s] = code;
         }
     }
+    // The cross-tile partial sums are stored compactly in fix-up order: sorted by DOF, then by
+    // tile; the partial of halo slot (t, s) goes to hdst[t][s], and DOF fix_g[r] adds the run
+    // [fix_off[r], fix_off[r+1]) of them to its owner's value, in ascending tile order.
     std::sort(halo_pairs.begin(), halo_pairs.end());
-    std::vector<uint32_t> fix_g, fix_off, fix_h;
-    fix_h.reserve(halo_pairs.size());
+    std::vector<uint32_t> fix_g, fix_off, hdst((size_t)c->ntiles * c->Spad, 0u);
     for (size_t i = 0; i < halo_pairs.size(); ++i) {
         const uint32_t g = (uint32_t)(halo_pairs[i] >> 32);
-        if (fix_g.empty() || fix_g.back() != g) { fix_g.push_back(g); fix_off.push_back((uint32_t)fix_h.size()); }
-        fix_h.push_back((uint32_t)(halo_pairs[i] & 0xFFFFFFFFu));
+        if (fix_g.empty() || fix_g.back() != g) { fix_g.push_back(g); fix_off.push_back((uint32_t)i); }
+        hdst[halo_pairs[i] & 0xFFFFFFFFu] = (uint32_t)i;
     }
-    fix_off.push_back((uint32_t)fix_h.size());
+    fix_off.push_back((uint32_t)halo_pairs.size());
     c->nfix = (int64_t)fix_g.size();
-    c->nfixh = (int64_t)fix_h.size();
+    c->nfixh = (int64_t)halo_pairs.size();
 
     // --- 1D rules and basis tables on [0,1] ---
     std::vector<double> gx, gw, nodes, val, der;
@@ -432,18 +434,16 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     CK(cudaMemcpy(c->d_slot, slot.data(), slot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_fix_g, fix_g.size()));
     CK(dalloc(c, &c->d_fix_off, fix_off.size()));
-    CK(dalloc(c, &c->d_fix_h, fix_h.size()));
-    if (!fix_g.empty()) {
-        CK(cudaMemcpy(c->d_fix_g, fix_g.data(), fix_g.size() * 4, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c->d_fix_h, fix_h.data(), fix_h.size() * 4, cudaMemcpyHostToDevice));
-    }
+    CK(dalloc(c, &c->d_hdst, hdst.size()));
+    CK(cudaMemcpy(c->d_hdst, hdst.data(), hdst.size() * 4, cudaMemcpyHostToDevice));
+    if (!fix_g.empty()) CK(cudaMemcpy(c->d_fix_g, fix_g.data(), fix_g.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_fix_off, fix_off.data(), fix_off.size() * 4, cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_vert, (size_t)nvert * dim));
     CK(cudaMemcpy(c->d_vert, mesh->vertices, (size_t)nvert * dim * sizeof(double), cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_geo, (size_t)c->nepad * c->NG * c->NQ));
     {
         double *h = nullptr;
-        CK(dalloc(c, &h, (size_t)c->ntiles * c->Spad));
+        CK(dalloc(c, &h, (size_t)c->nfixh));
         c->d_halo = h;
     }
     CK(dalloc(c, &c->d_err, 1));
@@ -477,7 +477,8 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     c->op.gt_off = c->d_gt_off; c->op.gt_src = c->d_gt_src; c->op.err = c->d_err;
     c->op.kr = c->d_kr; c->op.dkr = c->d_dkr; c->op.skip = nullptr;
     c->op.law_a = 0.5 * (prob->p - 2.0); c->op.eps2 = prob->eps * prob->eps;
-    c->fix.nfix = c->nfix; c->fix.fix_g = c->d_fix_g; c->fix.fix_off = c->d_fix_off; c->fix.fix_h = c->d_fix_h;
+    c->op.hdst = c->d_hdst;
+    c->fix.nfix = c->nfix; c->fix.fix_g = c->d_fix_g; c->fix.fix_off = c->d_fix_off;
     c->fix.skip = nullptr;
     CK(c->ops->prepare(c));
     CK(cudaDeviceSynchronize());
@@ -518,7 +519,7 @@ extern "C" fe_status fe_setup_ex(const fe_mesh *mesh, int order, int q1d, const 
 extern "C" void fe_destroy(fe_ctx *c)
 {
     if (!c) return;
-    void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_fix_off, c->d_fix_h, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
+    void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_fix_off, c->d_hdst, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
                      c->d_dkr, c->d_T64, c->d_T32, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
                      c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_state, c->w_partial };
     for (void *p : ptrs)
@@ -942,7 +943,7 @@ extern "C" fe_status fe_jacobian_action_noalloc(fe_ctx *c, const void *v, void *
     if (precision != 64 && precision != 32 && precision != -32)
         return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
     const size_t word = precision == 64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)c->ntiles * (size_t)c->Spad * word;
+    const size_t need = (size_t)c->nfixh * word;
     if (need > (size_t)FE_NOALLOC_SCRATCH_BYTES)
         return fail(c, FE_ERR_UNSUPPORTED,
                     "fe_jacobian_action_noalloc: problem needs %zu bytes of scratch, the static array holds %u",

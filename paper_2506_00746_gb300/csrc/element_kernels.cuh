@@ -162,15 +162,19 @@ __device__ __forceinline__ int64_t tq_stride(const OpParams &P)
     return sizeof(TC) == 8 ? P.tqs64 : P.tqs32;
 }
 
-// The stored tangent of a tile is [component][tile quadrature point], the tile's points numbered
-// lexicographically over the (k+1)T per direction lattice of the tile (x fastest); one component
-// block holds T^dim (k+1)^dim values.  Index of point q of the tile-local element at ec:
+// The stored tangent of a tile is [component][ex][qy_t][qz_t][qx]: per component, the tile's
+// quadrature points grouped by the element column ex along x, then the tile-level y and z point
+// indices (qy_t = ey (k+1) + qy, qz_t = ez (k+1) + qz), then the element-local qx (2D:
+// [component][ex][qy_t][qx]); one component block holds T^dim (k+1)^dim values.  Index of point
+// q of the tile-local element at ec:
 template <int DIM, int D1>
 __device__ __forceinline__ int tile_qp(const int (&ec)[3], int q, int T)
 {
     const int QT = D1 * T;
     const int qx = q % D1, qy = (q / D1) % D1, qz = DIM == 3 ? q / (D1 * D1) : 0;
-    return (ec[0] * D1 + qx) + QT * ((ec[1] * D1 + qy) + (DIM == 3 ? QT * (ec[2] * D1 + qz) : 0));
+    const int qyt = ec[1] * D1 + qy;
+    if (DIM == 3) return qx + D1 * ((ec[2] * D1 + qz) + QT * (qyt + QT * ec[0]));
+    return qx + D1 * (qyt + QT * ec[0]);
 }
 
 struct TileInfo {
@@ -305,7 +309,7 @@ __device__ __forceinline__ void scatter_tile(const OpParams &P, int64_t t, const
                 }
         const uint32_t g = code & SLOT_GMASK;
         if (code & SLOT_HALO) {
-            if (!(code & SLOT_ESS)) halo[t * P.Spad + s] = acc;
+            if (!(code & SLOT_ESS)) halo[P.hdst[t * P.Spad + s]] = acc;
         } else if (code & SLOT_ESS) {
             if (OUT == OUT_JV) y[g] = vorig[g];
             else if (OUT == OUT_RES) y[g] = TIO(0);
@@ -327,7 +331,7 @@ __global__ void k_fixup(const FixParams F, const TC *__restrict__ halo, TIO *__r
     const uint32_t g = F.fix_g[r];
     TC acc = (TC)y[g];
     const uint32_t j1 = F.fix_off[r + 1];
-    for (uint32_t j = F.fix_off[r]; j < j1; ++j) acc += halo[F.fix_h[j]];
+    for (uint32_t j = F.fix_off[r]; j < j1; ++j) acc += halo[j];
     y[g] = (TIO)acc;
 }
 
@@ -988,12 +992,13 @@ struct Ops {
         else { Tq = reinterpret_cast<const TC *>(c->d_T32); bs = reinterpret_cast<const BasisT<TC> *>(&c->b32); }
         const char *name = sizeof(TC) == 8 ? "jv_pa_f64" : "jv_pa_f32";
         if constexpr (DIM == 3) {
-            if (c->pipe_grid[variant<TC, TIO>()] > 0) {
+            const int grid = c->pipe_grid[variant<TC, TIO>()];
+            if (grid > 0) {
                 constexpr int TT = max_tile(3, D1 - 1);
-                const size_t tsm = tile_smem_bytes<D1, TT, TC>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32);
+                const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32, c->Spad);
                 {
                     LaunchScope ls(c, name, st);
-                    k_jv_tile<D1, TT, TC, TIO><<<(unsigned)c->ntiles, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                    k_jv_tile<D1, TT, TC, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(
                         c->op, *bs, Tq, v, y, reinterpret_cast<TC *>(c->d_halo));
                 }
                 fixup<TC, TIO>(c, y, st);
@@ -1021,7 +1026,7 @@ struct Ops {
         if constexpr (DIM == 3) {
             constexpr int TT = max_tile(3, D1 - 1);
             if (c->no_pipeline || c->T != TT) return cudaSuccess;
-            const size_t tsm = tile_smem_bytes<D1, TT, TC>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32);
+            const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32, c->Spad);
             if (tsm > (size_t)c->smem_optin) return cudaSuccess;
             cudaError_t e = raise_smem(k_jv_tile<D1, TT, TC, TIO>, tsm);
             if (e != cudaSuccess) return e;
@@ -1029,7 +1034,12 @@ struct Ops {
             e = cudaFuncGetAttributes(&fa, k_jv_tile<D1, TT, TC, TIO>);
             if (e != cudaSuccess) return e;
             if (fa.maxThreadsPerBlock < TileShape<D1, TT>::THREADS) return cudaSuccess;
-            c->pipe_grid[variant<TC, TIO>()] = 1;
+            int per_sm = 0;       // the launch must fit at least one CTA per SM
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jv_tile<D1, TT, TC, TIO>,
+                                                              TileShape<D1, TT>::THREADS, tsm);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1 || c->ntiles > 0x7fffffff) return cudaSuccess;
+            c->pipe_grid[variant<TC, TIO>()] = (int)c->ntiles;     // one CTA per tile
         }
         return cudaSuccess;
     }
@@ -1112,7 +1122,11 @@ struct Ops {
         if (e != cudaSuccess) return e;
         if ((e = prepare_tile<double, double>(c)) != cudaSuccess) return e;
         if ((e = prepare_tile<float, float>(c)) != cudaSuccess) return e;
-        return prepare_tile<float, double>(c);
+        if ((e = prepare_tile<float, double>(c)) != cudaSuccess) return e;
+        // the two FP32 variants must run the same kernel (the FP64-vector one is defined to give
+        // exactly the FP32 result): use the tile kernel for both or for neither
+        if (c->pipe_grid[1] == 0 || c->pipe_grid[2] == 0) c->pipe_grid[1] = c->pipe_grid[2] = 0;
+        return cudaSuccess;
     }
 
     static const OpTable *table()

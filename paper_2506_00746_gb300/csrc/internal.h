@@ -63,6 +63,7 @@ struct OpParams {
     int64_t tqs32;    // per-tile stride (floats) of the FP32 tangent, a multiple of 4
     int64_t tqs64;    // per-tile stride (doubles) of the FP64 tangent, a multiple of 2
     const uint32_t *slot;   // [ntiles][Spad]
+    const uint32_t *hdst;   // [ntiles][Spad]: position of a halo slot's partial sum in the halo array
     const uint16_t *gt_off; // in-tile G^T table: slot s sums Ye[gt_src[j]], j in [gt_off[s], gt_off[s+1])
     const uint16_t *gt_src; // (same for every tile; padded elements contribute exact zeros)
     int *err;               // device error word (bounded waits that time out set it)
@@ -74,12 +75,12 @@ struct OpParams {
     double eps2;      // eps^2
 };
 
-// Fix-up (deterministic G^T across tiles): y[fix_g[r]] += sum_j halo[fix_h[j]], j in [off[r], off[r+1])
+// Fix-up (deterministic G^T across tiles): y[fix_g[r]] += sum_j halo[j], j in [off[r], off[r+1]),
+// the partial sums of the non-owning tiles stored contiguously in ascending tile order
 struct FixParams {
     int64_t nfix;
     const uint32_t *fix_g;
     const uint32_t *fix_off;
-    const uint32_t *fix_h;
     const int *skip;
 };
 
@@ -149,7 +150,7 @@ struct fe_ctx {
 
     // device arrays
     uint32_t *d_slot = nullptr;
-    uint32_t *d_fix_g = nullptr, *d_fix_off = nullptr, *d_fix_h = nullptr;
+    uint32_t *d_fix_g = nullptr, *d_fix_off = nullptr, *d_hdst = nullptr;
     int64_t nfix = 0, nfixh = 0;
     double *d_vert = nullptr;
     double *d_geo = nullptr;
@@ -158,7 +159,7 @@ struct fe_ctx {
     double *d_T64 = nullptr;
     float *d_T32 = nullptr;
     double *d_diag = nullptr;
-    void *d_halo = nullptr;       // ntiles*S*8 bytes
+    void *d_halo = nullptr;       // nfixh * 8 bytes: cross-tile partial sums in fix-up order
     int *d_err = nullptr;
     bool lin64 = false, lin32 = false, have_diag = false;
 

@@ -5,20 +5,32 @@
 //     Bt[Q1 e + q][K e + a] = B^[q][a],   Gt[Q1 e + q][K e + a] = G^[q][a]   (e < TT, a <= K),
 // acting between the tile's SE = K TT + 1 DOF slots and QT = Q1 TT quadrature points per
 // direction.  Sum factorisation over the tile therefore applies B G to the tile's DOF block
-// directly (no per-element copies) and the transposed contractions apply G^T B^T: the DOF shared
-// by neighbouring elements of the tile receives both elements' terms inside the contraction, in
-// ascending element order, so the in-tile G^T is exact, deterministic and free.  Slots on the
-// tile's upper faces that belong to a neighbouring tile go to the halo buffer as before.
+// directly (no per-element copies), and the transposed contractions apply G^T B^T: a DOF shared
+// by two neighbouring elements of the tile receives both elements' terms, so the in-tile G^T
+// needs neither staging nor atomics.  Slots on the tile's upper faces that belong to a
+// neighbouring tile go to the halo buffer for the fix-up kernel.
+//
+// Threads: every line of a stage (e.g. the z-line of slots (sx, sy)) is split into its TT
+// element segments; segment h of all lines is handled by one group of warps (thread = line +
+// NLP * h), so the lanes of a warp walk consecutive lines.  A transposed stage leaves the seam
+// DOF between segments h and h+1 split: segment h+1's term in the array, segment h's term in a
+// small seam plane; the next stage adds them (left term first).  Shared-memory strides are
+// padded so that every access of a warp touches 32 distinct banks.
 //
 // Per CTA: one bulk copy (TMA, mbarrier-completed, bounded wait) brings the tile's stored
-// tangent block into shared memory while the threads gather the DOF block; then five line
-// stages (z, y, x+D+x^T, y^T, z^T), each thread owning one line of the current direction, with
-// shared-memory layouts chosen so that lanes of a warp touch consecutive or odd-strided words.
+// tangent block into shared memory while the threads gather the DOF block.
 #pragma once
 
 namespace feod {
 
 __host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// pad of the y-slot stride of the z/y-stage arrays that makes all their accesses bank-conflict
+// free (found by exhaustive search over the access patterns of this kernel)
+__host__ __device__ constexpr int tile_pad_a(int d1)
+{
+    return d1 == 2 ? 5 : d1 == 3 ? 8 : d1 == 4 ? 15 : d1 == 5 ? 15 : d1 == 6 ? 7 : 23;
+}
 
 template <int D1, int TT>
 struct TileShape {
@@ -27,17 +39,24 @@ struct TileShape {
     static constexpr int QT = D1 * TT;             // quadrature points per tile edge
     static constexpr int NS3 = SE * SE * SE;
     static constexpr int NQT = QT * QT * QT;
-    static constexpr int NA = SE * QT * SE;        // one z- or y-stage array
-    static constexpr int NC = QT * QT * SE;        // one x-stage array
-    static constexpr int THREADS = ((QT * QT + 31) / 32) * 32;
+    static constexpr int SA = SE * QT + tile_pad_a(D1);   // y-slot stride of A / E
+    static constexpr int NA = SA * SE;             // one z- or y-stage array (A, E)
+    static constexpr int NC = SE * QT * QT;        // one x-stage array (C, D)
+    static constexpr int NLP = ((QT * QT + 31) / 32) * 32;   // lines per segment group
+    static constexpr int THREADS = NLP * TT;
+    // seam planes (left terms of the DOFs shared by segments h and h+1)
+    static constexpr int NSX = (TT - 1) * QT * QT; // per x-stage array
+    static constexpr int NSY = (TT - 1) * QT * SE; // per y-stage array
+    static constexpr int NSZ = (TT - 1) * SE * SE;
 };
 
-template <int D1, int TT, typename TC>
-__host__ __device__ inline size_t tile_smem_bytes(int64_t tqs)
+template <int D1, int TT, typename TC, typename TIO>
+__host__ __device__ inline size_t tile_smem_bytes(int64_t tqs, int /*Spad*/)
 {
     using TS = TileShape<D1, TT>;
-    return 16 + pad16((size_t)tqs * sizeof(TC)) + pad16(TS::NS3 * sizeof(TC)) + pad16(TS::NS3 * 4) +
-           pad16(2 * (size_t)TS::NA * sizeof(TC)) + 3 * (size_t)TS::NC * sizeof(TC);
+    return 64 + pad16((size_t)tqs * sizeof(TC)) + 2 * pad16(TS::NS3 * 4) + pad16(TS::NS3 * sizeof(TIO)) +
+           pad16(2 * (size_t)TS::NA * sizeof(TC)) + pad16(3 * (size_t)TS::NC * sizeof(TC)) +
+           pad16((3 * (size_t)TS::NSX + 2 * (size_t)TS::NSY + (size_t)TS::NSZ) * sizeof(TC));
 }
 
 // n consecutive shared-memory values into registers; 16-byte vector loads when n % 4 == 0 (FP32)
@@ -63,14 +82,218 @@ __device__ __forceinline__ void lds_run(const TC *p, TC (&r)[N])
     }
 }
 
+// One tile from shared memory: z, y, x (+ D + x^T), y^T, z^T stages and the writes.  Tb: the
+// tile's tangent block, Vs: its gathered DOF block (I/O type), codes: its slot codes, hd: the
+// halo-array position of each halo slot's partial sum.
+template <int D1, int TT, typename TC, typename TIO>
+__device__ __forceinline__ void tile_stages(const OpParams &P, const BasisT<TC> &Bs, int64_t t, const TC *Tb,
+                                            const TIO *Vs, const uint32_t *codes, const uint32_t *hd, TC *AE,
+                                            TC *Cb, TC *SX, TC *SY, TC *SZ, const TIO *__restrict__ v,
+                                            TIO *__restrict__ y, TC *__restrict__ halo, int tid)
+{
+    using TS = TileShape<D1, TT>;
+    constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT;
+    constexpr int SA = TS::SA, NA = TS::NA, NC = TS::NC, NLP = TS::NLP;
+    constexpr int NSX = TS::NSX, NSY = TS::NSY;
+    const int L = tid % NLP, h = tid / NLP;     // line (lanes walk consecutive lines), segment
+
+    // z: segment h (element along z) of line (sx, sy): K+1 slots -> Q1 points, B^ and G^
+    if (L < SE * SE) {
+        const int sx = L % SE, sy = L / SE;
+        TC in[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) in[a] = (TC)Vs[((K * h + a) * SE + sy) * SE + sx];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            TC a0 = TC(0), a1 = TC(0);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) { a0 += Bs.B[q * D1 + a] * in[a]; a1 += Bs.G[q * D1 + a] * in[a]; }
+            const int o = sx + SE * (Q1 * h + q) + SA * sy;
+            AE[o] = a0;
+            AE[NA + o] = a1;
+        }
+    }
+    __syncthreads();
+    // y: segment h of line (sx, qz)
+    if (L < SE * QT) {
+        const int sx = L % SE, qz = L / SE;
+        TC a0[D1], a1[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) {
+            const int o = sx + SE * qz + SA * (K * h + a);
+            a0[a] = AE[o];
+            a1[a] = AE[NA + o];
+        }
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            TC c00 = TC(0), c01 = TC(0), c10 = TC(0);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                c00 += Bs.B[q * D1 + a] * a0[a];
+                c01 += Bs.G[q * D1 + a] * a0[a];
+                c10 += Bs.B[q * D1 + a] * a1[a];
+            }
+            const int o = sx + SE * qz + SE * QT * (Q1 * h + q);
+            Cb[o] = c00;
+            Cb[NC + o] = c01;
+            Cb[2 * NC + o] = c10;
+        }
+    }
+    __syncthreads();
+    // x: segment h (element column ex = h) of line (qy, qz): gradient, D, x transpose
+    TC d00[D1], d01[D1], d10[D1];
+    const bool actx = L < QT * QT;
+    const int xqz = L % QT, xqy = L / QT;
+    const int xo = SE * xqz + SE * QT * xqy + K * h;
+    if (actx) {
+        TC c00[D1], c01[D1], c10[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) {
+            c00[a] = Cb[xo + a]; c01[a] = Cb[NC + xo + a]; c10[a] = Cb[2 * NC + xo + a];
+            d00[a] = TC(0); d01[a] = TC(0); d10[a] = TC(0);
+        }
+        const TC *Tl = Tb + Q1 * (xqz + QT * (xqy + QT * h));
+        TC txx[Q1], tyy[Q1], tzz[Q1], txy[Q1], txz[Q1], tyz[Q1];
+        lds_run<Q1, TC>(Tl, txx);
+        lds_run<Q1, TC>(Tl + NQT, tyy);
+        lds_run<Q1, TC>(Tl + 2 * NQT, tzz);
+        lds_run<Q1, TC>(Tl + 3 * NQT, txy);
+        lds_run<Q1, TC>(Tl + 4 * NQT, txz);
+        lds_run<Q1, TC>(Tl + 5 * NQT, tyz);
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            TC gx = TC(0), gy = TC(0), gz = TC(0);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                gx += Bs.G[q * D1 + a] * c00[a];
+                gy += Bs.B[q * D1 + a] * c01[a];
+                gz += Bs.B[q * D1 + a] * c10[a];
+            }
+            const TC fx = txx[q] * gx + txy[q] * gy + txz[q] * gz;
+            const TC fy = txy[q] * gx + tyy[q] * gy + tyz[q] * gz;
+            const TC fz = txz[q] * gx + tyz[q] * gy + tzz[q] * gz;
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                d00[a] += Bs.G[q * D1 + a] * fx;
+                d01[a] += Bs.B[q * D1 + a] * fy;
+                d10[a] += Bs.B[q * D1 + a] * fz;
+            }
+        }
+    }
+    __syncthreads();       // every segment has read its c values before any is overwritten
+    if (actx) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) { Cb[xo + a] = d00[a]; Cb[NC + xo + a] = d01[a]; Cb[2 * NC + xo + a] = d10[a]; }
+        if (h == TT - 1) {
+            Cb[xo + K] = d00[K]; Cb[NC + xo + K] = d01[K]; Cb[2 * NC + xo + K] = d10[K];
+        } else {
+            const int so = h * QT * QT + L;
+            SX[so] = d00[K]; SX[NSX + so] = d01[K]; SX[2 * NSX + so] = d10[K];
+        }
+    }
+    __syncthreads();
+    // y transpose: segment h (element along y) of line (sx, qz)
+    if (L < SE * QT) {
+        const int sx = L % SE, qz = L / SE;
+        const bool xseam = (sx % K == 0) && sx > 0 && sx < SE - 1;
+        TC e00[Q1], e01[Q1], e10[Q1];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            const int qy = Q1 * h + q;
+            const int o = sx + SE * qz + SE * QT * qy;
+            e00[q] = Cb[o]; e01[q] = Cb[NC + o]; e10[q] = Cb[2 * NC + o];
+            if (xseam) {
+                const int so = (sx / K - 1) * QT * QT + qz + QT * qy;
+                e00[q] = SX[so] + e00[q]; e01[q] = SX[NSX + so] + e01[q]; e10[q] = SX[2 * NSX + so] + e10[q];
+            }
+        }
+        TC E0[D1], E1[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) { E0[a] = TC(0); E1[a] = TC(0); }
+#pragma unroll
+        for (int q = 0; q < Q1; ++q)
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                E0[a] += Bs.B[q * D1 + a] * e00[q] + Bs.G[q * D1 + a] * e01[q];
+                E1[a] += Bs.B[q * D1 + a] * e10[q];
+            }
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            const int o = sx + SE * qz + SA * (K * h + a);
+            AE[o] = E0[a];
+            AE[NA + o] = E1[a];
+        }
+        if (h == TT - 1) {
+            const int o = sx + SE * qz + SA * (SE - 1);
+            AE[o] = E0[K];
+            AE[NA + o] = E1[K];
+        } else {
+            const int so = h * QT * SE + L;
+            SY[so] = E0[K];
+            SY[NSY + so] = E1[K];
+        }
+    }
+    __syncthreads();
+    // z transpose: segment h (element along z) of line (sx, sy); P^T and the writes
+    TC out[D1];
+    const bool actz = L < SE * SE;
+    const int zx = L % SE, zy = L / SE;
+    auto write_slot = [&](int sz, TC val) {
+        const int s = (sz * SE + zy) * SE + zx;
+        const uint32_t code = codes[s];
+        if (code == SLOT_INVALID) return;
+        const uint32_t g = code & SLOT_GMASK;
+        if (code & SLOT_HALO) {
+            if (!(code & SLOT_ESS)) halo[hd[s]] = val;
+        } else if (code & SLOT_ESS) {
+            y[g] = v[g];
+        } else {
+            y[g] = (TIO)val;
+        }
+    };
+    if (actz) {
+        const bool yseam = (zy % K == 0) && zy > 0 && zy < SE - 1;
+        TC z0[Q1], z1[Q1];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            const int qz = Q1 * h + q;
+            const int o = zx + SE * qz + SA * zy;
+            z0[q] = AE[o];
+            z1[q] = AE[NA + o];
+            if (yseam) {
+                const int so = (zy / K - 1) * QT * SE + zx + SE * qz;
+                z0[q] = SY[so] + z0[q];
+                z1[q] = SY[NSY + so] + z1[q];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < D1; ++a) out[a] = TC(0);
+#pragma unroll
+        for (int q = 0; q < Q1; ++q)
+#pragma unroll
+            for (int a = 0; a < D1; ++a) out[a] += Bs.B[q * D1 + a] * z0[q] + Bs.G[q * D1 + a] * z1[q];
+        // slots that only this segment touches
+#pragma unroll
+        for (int a = 1; a < K; ++a) write_slot(K * h + a, out[a]);
+        if (h == 0) write_slot(0, out[0]);
+        if (h == TT - 1) write_slot(SE - 1, out[K]);
+        else SZ[h * SE * SE + L] = out[K];
+    }
+    __syncthreads();
+    // z seams: left segment's term, then this segment's
+    if (actz && h > 0) write_slot(K * h, SZ[(h - 1) * SE * SE + L] + out[0]);
+}
+
+// One CTA per tile.  Thread 0 starts the bulk copy of the tile's tangent block; meanwhile all
+// threads load the slot codes, then (in one batch) the input values and, for halo slots, their
+// halo-array positions.
 template <int D1, int TT, typename TC, typename TIO>
 __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     k_jv_tile(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs, const TC *__restrict__ Tq,
               const TIO *__restrict__ v, TIO *__restrict__ y, TC *__restrict__ halo)
 {
     using TS = TileShape<D1, TT>;
-    constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NS3 = TS::NS3, NQT = TS::NQT;
-    constexpr int NA = TS::NA, NC = TS::NC, NTH = TS::THREADS;
+    constexpr int NS3 = TS::NS3, NA = TS::NA, NC = TS::NC, NSX = TS::NSX, NSY = TS::NSY, NTH = TS::THREADS;
     if (P.skip && *P.skip) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int64_t t = blockIdx.x;
@@ -79,205 +302,57 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     const uint32_t tq_bytes = (uint32_t)(tqs * sizeof(TC));
 
     unsigned char *p = smem;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(p);    p += 16;
-    TC *Tb = reinterpret_cast<TC *>(p);                 p += pad16(tq_bytes);            // [c][qz][qy][qx]
-    TC *Vs = reinterpret_cast<TC *>(p);                 p += pad16(NS3 * sizeof(TC));    // [sz][sy][sx]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(p);    p += 64;
+    TC *Tb = reinterpret_cast<TC *>(p);                 p += pad16(tq_bytes);
     uint32_t *codes = reinterpret_cast<uint32_t *>(p);  p += pad16(NS3 * 4);
-    TC *AE = reinterpret_cast<TC *>(p);                 p += pad16(2 * NA * sizeof(TC)); // [arr][sy][qz][sx]
-    TC *Cb = reinterpret_cast<TC *>(p);                                                   // [arr][qz][qy][sx]
+    uint32_t *hd = reinterpret_cast<uint32_t *>(p);     p += pad16(NS3 * 4);
+    TIO *Vs = reinterpret_cast<TIO *>(p);               p += pad16(NS3 * sizeof(TIO));
+    TC *AE = reinterpret_cast<TC *>(p);                 p += pad16(2 * (size_t)NA * sizeof(TC));
+    TC *Cb = reinterpret_cast<TC *>(p);                 p += pad16(3 * (size_t)NC * sizeof(TC));
+    TC *SX = reinterpret_cast<TC *>(p);
+    TC *SY = SX + 3 * NSX;
+    TC *SZ = SY + 2 * NSY;
 
-    // the tile's tangent block: one bulk copy, in flight while the DOF block is gathered
     if (tid == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
         mbar_arrive_expect_tx(mbar, tq_bytes);
         tma_load_1d(Tb, Tq + t * tqs, tq_bytes, mbar);
     }
-    // G and P: slot codes, then all of this thread's input values at once
     {
         constexpr int NPER = (NS3 + NTH - 1) / NTH;
         const uint32_t *sl = P.slot + t * P.Spad;
-        uint32_t cr[NPER];
+        const uint32_t *hs = P.hdst + t * P.Spad;
+        uint32_t cr[NPER], hr[NPER];
 #pragma unroll
         for (int i = 0; i < NPER; ++i) {
             const int s = tid + i * NTH;
             cr[i] = s < NS3 ? sl[s] : SLOT_INVALID;
         }
-        TC vr[NPER];
+        TIO vr[NPER];
 #pragma unroll
-        for (int i = 0; i < NPER; ++i) vr[i] = (cr[i] & SLOT_ESS) ? TC(0) : (TC)v[cr[i] & SLOT_GMASK];
+        for (int i = 0; i < NPER; ++i) {
+            vr[i] = (cr[i] & SLOT_ESS) ? TIO(0) : v[cr[i] & SLOT_GMASK];
+            hr[i] = (cr[i] & SLOT_HALO) && !(cr[i] & SLOT_ESS) ? hs[tid + i * NTH] : 0u;
+        }
 #pragma unroll
         for (int i = 0; i < NPER; ++i) {
             const int s = tid + i * NTH;
-            if (s < NS3) { codes[s] = cr[i]; Vs[s] = vr[i]; }
+            if (s < NS3) { codes[s] = cr[i]; Vs[s] = vr[i]; hd[s] = hr[i]; }
         }
     }
+    // makes thread 0's mbarrier initialisation (and the gathered block) visible before any thread
+    // polls the barrier
     __syncthreads();
-
-    // z: line (sx, sy) of SE slots -> QT points, B^ and G^
-    if (tid < SE * SE) {
-        const int sx = tid % SE, sy = tid / SE;
-        TC in[SE];
-#pragma unroll
-        for (int sz = 0; sz < SE; ++sz) in[sz] = Vs[(sz * SE + sy) * SE + sx];
-#pragma unroll
-        for (int e = 0; e < TT; ++e)
-#pragma unroll
-            for (int q = 0; q < Q1; ++q) {
-                TC a0 = TC(0), a1 = TC(0);
-#pragma unroll
-                for (int a = 0; a < D1; ++a) {
-                    a0 += Bs.B[q * D1 + a] * in[K * e + a];
-                    a1 += Bs.G[q * D1 + a] * in[K * e + a];
-                }
-                const int o = (sy * QT + Q1 * e + q) * SE + sx;
-                AE[o] = a0;
-                AE[NA + o] = a1;
-            }
-    }
-    __syncthreads();
-    // y: line (sx, qz)
-    if (tid < SE * QT) {
-        const int sx = tid % SE, qz = tid / SE;
-        TC a0[SE], a1[SE];
-#pragma unroll
-        for (int sy = 0; sy < SE; ++sy) {
-            a0[sy] = AE[(sy * QT + qz) * SE + sx];
-            a1[sy] = AE[NA + (sy * QT + qz) * SE + sx];
-        }
-#pragma unroll
-        for (int e = 0; e < TT; ++e)
-#pragma unroll
-            for (int q = 0; q < Q1; ++q) {
-                TC c00 = TC(0), c01 = TC(0), c10 = TC(0);
-#pragma unroll
-                for (int a = 0; a < D1; ++a) {
-                    c00 += Bs.B[q * D1 + a] * a0[K * e + a];
-                    c01 += Bs.G[q * D1 + a] * a0[K * e + a];
-                    c10 += Bs.B[q * D1 + a] * a1[K * e + a];
-                }
-                const int o = (qz * QT + Q1 * e + q) * SE + sx;
-                Cb[o] = c00;
-                Cb[NC + o] = c01;
-                Cb[2 * NC + o] = c10;
-            }
-    }
-    // the tangent block must have landed (bounded wait; uniform decision, doubles as the barrier)
-    const bool bad = !mbar_wait_bounded(mbar, 0);
-    if (__syncthreads_or(bad)) {
+    // the tangent block must have landed (bounded wait; uniform decision)
+    if (__syncthreads_or(!mbar_wait_bounded(mbar, 0))) {
         if (tid == 0) {
             atomicExch(P.err, 3);
             mbar_wait_bounded(mbar, 0);
         }
         return;
     }
-    // x: line (qy, qz); gradient, D (stored tangent), and the x transpose, element by element
-    if (tid < QT * QT) {
-        const int qy = tid % QT, qz = tid / QT;
-        const int o = (qz * QT + qy) * SE;
-        TC c00[SE], c01[SE], c10[SE], d00[SE], d01[SE], d10[SE];
-#pragma unroll
-        for (int sx = 0; sx < SE; ++sx) {
-            c00[sx] = Cb[o + sx]; c01[sx] = Cb[NC + o + sx]; c10[sx] = Cb[2 * NC + o + sx];
-            d00[sx] = TC(0); d01[sx] = TC(0); d10[sx] = TC(0);
-        }
-        const TC *Tl = Tb + (qz * QT + qy) * QT;
-#pragma unroll
-        for (int e = 0; e < TT; ++e) {
-            TC txx[Q1], tyy[Q1], tzz[Q1], txy[Q1], txz[Q1], tyz[Q1];
-            lds_run<Q1, TC>(Tl + Q1 * e, txx);
-            lds_run<Q1, TC>(Tl + NQT + Q1 * e, tyy);
-            lds_run<Q1, TC>(Tl + 2 * NQT + Q1 * e, tzz);
-            lds_run<Q1, TC>(Tl + 3 * NQT + Q1 * e, txy);
-            lds_run<Q1, TC>(Tl + 4 * NQT + Q1 * e, txz);
-            lds_run<Q1, TC>(Tl + 5 * NQT + Q1 * e, tyz);
-#pragma unroll
-            for (int q = 0; q < Q1; ++q) {
-                TC gx = TC(0), gy = TC(0), gz = TC(0);
-#pragma unroll
-                for (int a = 0; a < D1; ++a) {
-                    gx += Bs.G[q * D1 + a] * c00[K * e + a];
-                    gy += Bs.B[q * D1 + a] * c01[K * e + a];
-                    gz += Bs.B[q * D1 + a] * c10[K * e + a];
-                }
-                const TC fx = txx[q] * gx + txy[q] * gy + txz[q] * gz;
-                const TC fy = txy[q] * gx + tyy[q] * gy + tyz[q] * gz;
-                const TC fz = txz[q] * gx + tyz[q] * gy + tzz[q] * gz;
-#pragma unroll
-                for (int a = 0; a < D1; ++a) {
-                    d00[K * e + a] += Bs.G[q * D1 + a] * fx;
-                    d01[K * e + a] += Bs.B[q * D1 + a] * fy;
-                    d10[K * e + a] += Bs.B[q * D1 + a] * fz;
-                }
-            }
-        }
-#pragma unroll
-        for (int sx = 0; sx < SE; ++sx) {
-            Cb[o + sx] = d00[sx]; Cb[NC + o + sx] = d01[sx]; Cb[2 * NC + o + sx] = d10[sx];
-        }
-    }
-    __syncthreads();
-    // y transpose: line (sx, qz)
-    if (tid < SE * QT) {
-        const int sx = tid % SE, qz = tid / SE;
-        TC e00[QT], e01[QT], e10[QT], E0[SE], E1[SE];
-#pragma unroll
-        for (int qy = 0; qy < QT; ++qy) {
-            const int o = (qz * QT + qy) * SE + sx;
-            e00[qy] = Cb[o]; e01[qy] = Cb[NC + o]; e10[qy] = Cb[2 * NC + o];
-        }
-#pragma unroll
-        for (int s = 0; s < SE; ++s) { E0[s] = TC(0); E1[s] = TC(0); }
-#pragma unroll
-        for (int e = 0; e < TT; ++e)
-#pragma unroll
-            for (int q = 0; q < Q1; ++q)
-#pragma unroll
-                for (int a = 0; a < D1; ++a) {
-                    E0[K * e + a] += Bs.B[q * D1 + a] * e00[Q1 * e + q] + Bs.G[q * D1 + a] * e01[Q1 * e + q];
-                    E1[K * e + a] += Bs.B[q * D1 + a] * e10[Q1 * e + q];
-                }
-#pragma unroll
-        for (int sy = 0; sy < SE; ++sy) {
-            const int o = (sy * QT + qz) * SE + sx;
-            AE[o] = E0[sy];
-            AE[NA + o] = E1[sy];
-        }
-    }
-    __syncthreads();
-    // z transpose: line (sx, sy); then P^T and the writes (halo slots to the fix-up buffer)
-    if (tid < SE * SE) {
-        const int sx = tid % SE, sy = tid / SE;
-        TC z0[QT], z1[QT], out[SE];
-#pragma unroll
-        for (int qz = 0; qz < QT; ++qz) {
-            z0[qz] = AE[(sy * QT + qz) * SE + sx];
-            z1[qz] = AE[NA + (sy * QT + qz) * SE + sx];
-        }
-#pragma unroll
-        for (int s = 0; s < SE; ++s) out[s] = TC(0);
-#pragma unroll
-        for (int e = 0; e < TT; ++e)
-#pragma unroll
-            for (int q = 0; q < Q1; ++q)
-#pragma unroll
-                for (int a = 0; a < D1; ++a)
-                    out[K * e + a] += Bs.B[q * D1 + a] * z0[Q1 * e + q] + Bs.G[q * D1 + a] * z1[Q1 * e + q];
-#pragma unroll
-        for (int sz = 0; sz < SE; ++sz) {
-            const int s = (sz * SE + sy) * SE + sx;
-            const uint32_t code = codes[s];
-            if (code == SLOT_INVALID) continue;
-            const uint32_t g = code & SLOT_GMASK;
-            if (code & SLOT_HALO) {
-                if (!(code & SLOT_ESS)) halo[t * P.Spad + s] = out[sz];
-            } else if (code & SLOT_ESS) {
-                y[g] = v[g];
-            } else {
-                y[g] = (TIO)out[sz];
-            }
-        }
-    }
+    tile_stages<D1, TT, TC, TIO>(P, Bs, t, Tb, Vs, codes, hd, AE, Cb, SX, SY, SZ, v, y, halo, tid);
 }
 
 }  // namespace feod

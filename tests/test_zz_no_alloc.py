@@ -53,12 +53,12 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch():
     import torch
     from paper_2506_00746_gb300 import Operator, abi
     lib = abi.library()
-    op = Operator(3, 48, 3, I.lattice_vertices(3, 48, seed=0), p=3.0)   # 13,824 tiles x 343 slots
-    op.linearize(torch.from_numpy(I.smooth_field(3, 48, 3, seed=1)).cuda())
-    v = torch.zeros(op.n_dofs, dtype=torch.float32, device="cuda")
+    op = Operator(3, 56, 3, I.lattice_vertices(3, 56, seed=0), p=3.0)   # ~2.7M cross-tile partial sums
+    op.linearize(torch.from_numpy(I.smooth_field(3, 56, 3, seed=1)).cuda())
+    v = torch.zeros(op.n_dofs, dtype=torch.float64, device="cuda")
     y = torch.zeros_like(v)
-    st = lib.fe_jacobian_action_noalloc(op.ctx, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(y.data_ptr()), 32,
+    st = lib.fe_jacobian_action_noalloc(op.ctx, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(y.data_ptr()), 64,
                                         abi.stream_handle())
-    assert st == 5
+    assert st == 5                                                        # 8-byte words exceed 16 MiB
     assert "static array holds" in abi.fe_last_error(op.ctx)
     op.close()
