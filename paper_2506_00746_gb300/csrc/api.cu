@@ -150,6 +150,10 @@ fe_status ensure_work(fe_ctx *c)
     CK(dalloc(c, &c->w_cr, n));
     CK(dalloc(c, &c->w_cp, n));
     CK(dalloc(c, &c->w_cq, n));
+    CK(dalloc(c, &c->w_fx, n));
+    CK(dalloc(c, &c->w_fr, n));
+    CK(dalloc(c, &c->w_fp, n));
+    CK(dalloc(c, &c->w_fq, n));
     CgState *s = nullptr;
     CK(dalloc(c, &s, 2));
     CK(cudaMemset(s, 0, 2 * sizeof(CgState)));
@@ -204,7 +208,8 @@ fe_status apply_jv_cached(fe_ctx *c, const void *v, void *y, int precision, cuda
 }
 
 // Enqueue `m` CG iterations (J p, alpha, update, direction); every kernel is a no-op once the
-// device flag `done` is set.
+// device flag `done` is set.  precision 64: FP64 operator and vectors; 32: FP32 operator and
+// vectors (CG scalars and inner-product sums in FP64).
 void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
 {
     CgState *s = cg_state(c);
@@ -212,11 +217,17 @@ void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
     c->op.skip = &s->done;
     c->fix.skip = &s->done;
     for (int i = 0; i < m; ++i) {
-        if (precision == 64) c->ops->jv_pa_64(c, c->w_cp, c->w_cq, st);
-        else c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
-        { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
-        { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv, n, s, c->w_partial); }
-        { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cp, c->w_cr, c->w_dinv, n, s); }
+        if (precision == 64) {
+            c->ops->jv_pa_64(c, c->w_cp, c->w_cq, st);
+            { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
+            { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv, n, s, c->w_partial); }
+            { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cp, c->w_cr, c->w_dinv, n, s); }
+        } else {
+            c->ops->jv_pa_32(c, c->w_fp, c->w_fq, st);
+            { LaunchScope ls(c, "cg_alpha32", st); k_cg_alpha32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_fp, c->w_fq, n, s, c->w_partial); }
+            { LaunchScope ls(c, "cg_update32", st); k_cg_update32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_fx, c->w_fr, c->w_fp, c->w_fq, c->w_dinv, n, s, c->w_partial); }
+            { LaunchScope ls(c, "cg_direction32", st); k_cg_direction32<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_fp, c->w_fr, c->w_dinv, n, s); }
+        }
     }
     c->op.skip = nullptr;
     c->fix.skip = nullptr;
@@ -228,10 +239,20 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
 {
     cudaStream_t st = c->own_stream;
     CgState *s = cg_state(c);
-    {
+    if (precision == 64) {
         LaunchScope ls(c, "cg_init", st);
         k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->nl, s, rtol,
                                                       max_iter, c->w_partial);
+    } else {
+        CgState *ds = s + 1;
+        {
+            LaunchScope ls(c, "dot", st);
+            k_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, b, c->nl, c->w_partial + 2 * RED_BLOCKS, &ds->counter,
+                                                      &ds->scalar);
+        }
+        LaunchScope ls(c, "cg_init32", st);
+        k_cg_init32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv, c->w_fx, c->w_fr, c->w_fp, c->nl, s,
+                                                        &ds->scalar, rtol, max_iter, c->w_partial);
     }
     CKLAUNCH();
     if (batch < 1) batch = 1;
@@ -267,6 +288,12 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
         CK(cudaStreamSynchronize(st));
         if (h->done) break;
     }
+    if (precision != 64) {
+        // the FP32 solution, unscaled, into the FP64 solution vector
+        LaunchScope ls(c, "cg_widen", st);
+        k_cg_widen<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cx, c->w_fx, c->nl, s);
+    }
+    CKLAUNCH();
     if (iters) *iters = h->iter;
     if (done_code) *done_code = h->done;
     return FE_OK;
@@ -521,7 +548,7 @@ extern "C" void fe_destroy(fe_ctx *c)
     if (!c) return;
     void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_fix_off, c->d_hdst, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
                      c->d_dkr, c->d_T64, c->d_T32, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
-                     c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_state, c->w_partial };
+                     c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_fx, c->w_fr, c->w_fp, c->w_fq, c->w_state, c->w_partial };
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
@@ -728,7 +755,7 @@ extern "C" fe_status fe_cg_solve(fe_ctx *c, const double *b, double *x, double r
     }
     CKLAUNCH();
     int it = 0, done = 0;
-    s = run_cg(c, b, rtol, max_iter, precision == 64 ? 64 : -32, 16, true, &it, &done);
+    s = run_cg(c, b, rtol, max_iter, precision, 16, true, &it, &done);
     if (s != FE_OK) return s;
     CK(cudaMemcpyAsync(x, c->w_cx, (size_t)c->nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
@@ -777,7 +804,7 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
     double cg_ms = 0.0;
     double *T64 = mixed ? nullptr : c->d_T64;
     float *T32 = mixed ? c->d_T32 : nullptr;
-    const int jprec = mixed ? -32 : 64;
+    const int jprec = mixed ? 32 : 64;
 
     // R and J_D at u (fused)
     c->ops->residual(c, u, c->w_r, T64, T32, st);

@@ -132,8 +132,8 @@ struct fe_ctx {
     int Spad = 0;                               // per-tile slot stride
     int64_t tqs32 = 0, tqs64 = 0;               // per-tile tangent strides (elements)
     uint16_t *d_gt_off = nullptr, *d_gt_src = nullptr;   // in-tile G^T table
-    // persistent grid of the pipelined 3D J v kernels per variant [FP64, FP32, FP32 with FP64
-    // vectors]; 0 = use the one-CTA-per-tile kernel
+    // grid (= number of tiles) of the tile-level 3D J v kernel per variant [FP64, FP32, FP32 with
+    // FP64 vectors]; 0 = that variant runs the per-element kernel
     int pipe_grid[3] = { 0, 0, 0 };
     bool no_pipeline = false;
     int smem_optin = 0;
@@ -164,13 +164,15 @@ struct fe_ctx {
     bool lin64 = false, lin32 = false, have_diag = false;
 
     // Newton / CG work space (allocated on first use)
-    double *w_r = nullptr, *w_d = nullptr, *w_trial = nullptr, *w_dinv = nullptr;
-    double *w_cx = nullptr, *w_cr = nullptr, *w_cp = nullptr, *w_cq = nullptr;
+    double *w_r = nullptr, *w_d = nullptr, *w_trial = nullptr;
+    float *w_dinv = nullptr;      // Jacobi scaling 1/diag(J), FP32
+    double *w_cx = nullptr, *w_cr = nullptr, *w_cp = nullptr, *w_cq = nullptr;   // FP64 CG
+    float *w_fx = nullptr, *w_fr = nullptr, *w_fp = nullptr, *w_fq = nullptr;    // FP32 CG
     void *w_state = nullptr;      // device CG state
     double *w_partial = nullptr;  // reduction partials
     void *h_state = nullptr;      // pinned host mirror
     cudaStream_t own_stream = nullptr;
-    // captured CG batches, [0] FP64 operator, [1] FP32 operator with FP64 vectors
+    // captured CG batches, [0] FP64 operator and vectors, [1] FP32 operator and vectors
     cudaGraphExec_t cg_exec[2] = { nullptr, nullptr };
     int cg_batch[2] = { 0, 0 };
     int64_t cg_launches[2] = { 0, 0 };

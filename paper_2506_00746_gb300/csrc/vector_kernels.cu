@@ -225,14 +225,14 @@ __global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b
 }
 
 // CG start (x = 0): r = b, p = z = dinv b; rz = r.z, rr = r.r; tol2 = rtol^2 rr.
-__global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, double *__restrict__ x,
+__global__ void k_cg_init(const double *__restrict__ b, const float *__restrict__ dinv, double *__restrict__ x,
                           double *__restrict__ r, double *__restrict__ p, int64_t n, CgState *st, double rtol,
                           int max_iter, double *partial)
 {
     __shared__ double sh[RED_THREADS];
     double s[2] = { 0.0, 0.0 };
     for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
-        const double bi = b[i], zi = dinv[i] * bi;
+        const double bi = b[i], zi = (double)dinv[i] * bi;
         x[i] = 0.0; r[i] = bi; p[i] = zi;
         s[0] += bi * zi; s[1] += bi * bi;
     }
@@ -265,7 +265,7 @@ __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restric
 
 // x += alpha p; r -= alpha q; z = dinv r; rz' = r.z, rr = r.r; beta = rz'/rz; convergence test.
 __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, CgState *st,
+                            const double *__restrict__ q, const float *__restrict__ dinv, int64_t n, CgState *st,
                             double *partial)
 {
     if (st->done) return;
@@ -276,7 +276,7 @@ __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, cons
         x[i] += alpha * p[i];
         const double ri = r[i] - alpha * q[i];
         r[i] = ri;
-        s[0] += ri * dinv[i] * ri; s[1] += ri * ri;
+        s[0] += ri * (double)dinv[i] * ri; s[1] += ri * ri;
     }
     double o[2];
     if (last_block_sum<2>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
@@ -290,13 +290,13 @@ __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, cons
 }
 
 // p = dinv r + beta p (skipped once converged).
-__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
+__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const float *__restrict__ dinv,
                                int64_t n, const CgState *st)
 {
     if (st->done) return;
     const double beta = st->beta;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = dinv[i] * r[i] + beta * p[i];
+        p[i] = (double)dinv[i] * r[i] + beta * p[i];
 }
 
 // y = a + alpha b
@@ -314,13 +314,177 @@ __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, do
         y[i] = alpha * x[i];
 }
 
-// y = 1 / x (Jacobi preconditioner from the assembled diagonal)
-__global__ void k_reciprocal(double *__restrict__ y, const double *__restrict__ x, int64_t n)
+// y = 1 / x rounded to FP32 (Jacobi preconditioner from the assembled diagonal)
+__global__ void k_reciprocal(float *__restrict__ y, const double *__restrict__ x, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double d = x[i];
-        y[i] = d != 0.0 ? 1.0 / d : 1.0;
+        y[i] = (float)(d != 0.0 ? 1.0 / d : 1.0);
     }
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP32 CG (vectors and operator in FP32, CG scalars in FP64)
+// ------------------------------------------------------------------------------------------------
+// Knuth's TwoSum and the FMA form of TwoProduct are error-free transformations (a + b = s + e and
+// a b = p + e exactly in round-to-nearest); carrying the rounding errors in a second word gives
+// the compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005),
+// accurate as if accumulated in twice the working precision.  The _rn intrinsics keep the
+// compiler from contracting or reordering the steps.  This keeps the FP32 CG's inner products on
+// the FP32 pipes (the FP64 rate of the part is a small fraction of its FP32 rate).
+struct Acc2 {
+    float s = 0.0f, c = 0.0f;
+};
+
+__device__ __forceinline__ void acc2(Acc2 &a, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    const float s = __fadd_rn(a.s, p);
+    const float z = __fsub_rn(s, a.s);
+    const float se = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, z)), __fsub_rn(p, z));
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fadd_rn(pe, se));
+}
+
+__device__ __forceinline__ double acc2_value(const Acc2 &a) { return (double)a.s + (double)a.c; }
+
+// Index ranges of the FP32 vector kernels: float4 groups i in [0, n/4) grid-strided, then the
+// n mod 4 tail elements, each in a fixed thread, so the accumulation order is fixed.
+struct Stride4 {
+    int64_t g0, gs, n4;
+    __device__ Stride4(int64_t n)
+        : g0((int64_t)blockIdx.x * blockDim.x + threadIdx.x), gs((int64_t)gridDim.x * blockDim.x), n4(n >> 2) {}
+};
+
+// Power-of-two scaling of the right-hand side (exact): b / 2^e with 2^e near the RMS of b, so
+// the FP32 vectors stay far from the FP32 underflow and overflow thresholds.
+__device__ __forceinline__ int cg_scale_exp(double bb, int64_t n)
+{
+    int e = 0;
+    if (bb > 0.0 && isfinite(bb)) frexp(sqrt(bb / (double)n), &e);
+    return e;
+}
+
+// CG start (x = 0) in FP32: r = b / 2^e, p = z = dinv r; rz = r.z, rr = r.r; tol2 = rtol^2 rr.
+// bb = b.b (FP64, computed by k_dot before this kernel).
+__global__ void __launch_bounds__(RED_THREADS) k_cg_init32(const double *__restrict__ b,
+                                                           const float *__restrict__ dinv, float *__restrict__ x,
+                                                           float *__restrict__ r, float *__restrict__ p, int64_t n,
+                                                           CgState *st, const double *bb, double rtol, int max_iter,
+                                                           double *partial)
+{
+    __shared__ double sh[RED_THREADS];
+    const int e = cg_scale_exp(*bb, n);
+    Acc2 rz, rr;
+    const Stride4 I(n);
+    for (int64_t i = I.g0; i < n; i += I.gs) {
+        const float ri = (float)ldexp(b[i], -e);
+        const float zi = __fmul_rn(dinv[i], ri);
+        x[i] = 0.0f; r[i] = ri; p[i] = zi;
+        acc2(rz, ri, zi); acc2(rr, ri, ri);
+    }
+    double s[2] = { acc2_value(rz), acc2_value(rr) }, o[2];
+    if (last_block_sum<2>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+        st->scale_exp = e;
+        st->rz = o[0]; st->rr = o[1]; st->rr0 = o[1];
+        st->tol2 = rtol * rtol * o[1];
+        st->iter = 0; st->max_iter = max_iter;
+        st->done = (o[1] <= st->tol2 || o[1] == 0.0) ? CG_CONVERGED : (isfinite(o[1]) ? 0 : CG_NAN);
+        if (max_iter <= 0 && !st->done) st->done = CG_MAXIT;
+    }
+}
+
+// alpha = rz / (p.q) with p.q by Dot2; breakdown when p.q <= 0 or not finite.
+__global__ void __launch_bounds__(RED_THREADS) k_cg_alpha32(const float *__restrict__ p,
+                                                            const float *__restrict__ q, int64_t n, CgState *st,
+                                                            double *partial)
+{
+    if (st->done) return;
+    __shared__ double sh[RED_THREADS];
+    Acc2 pq;
+    const Stride4 I(n);
+    const float4 *p4 = reinterpret_cast<const float4 *>(p), *q4 = reinterpret_cast<const float4 *>(q);
+    for (int64_t i = I.g0; i < I.n4; i += I.gs) {
+        const float4 a = p4[i], b = q4[i];
+        acc2(pq, a.x, b.x); acc2(pq, a.y, b.y); acc2(pq, a.z, b.z); acc2(pq, a.w, b.w);
+    }
+    for (int64_t i = 4 * I.n4 + I.g0; i < n; i += I.gs) acc2(pq, p[i], q[i]);
+    double s[1] = { acc2_value(pq) }, o[1];
+    if (last_block_sum<1>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+        st->pq = o[0];
+        if (!(o[0] > 0.0) || !isfinite(o[0])) { st->done = CG_BREAKDOWN; st->alpha = 0.0; }
+        else st->alpha = st->rz / o[0];
+    }
+}
+
+// x += alpha p; r -= alpha q; z = dinv r; rz' = r.z, rr = r.r (Dot2); beta = rz'/rz; convergence.
+__global__ void __launch_bounds__(RED_THREADS) k_cg_update32(float *__restrict__ x, float *__restrict__ r,
+                                                             const float *__restrict__ p,
+                                                             const float *__restrict__ q,
+                                                             const float *__restrict__ dinv, int64_t n, CgState *st,
+                                                             double *partial)
+{
+    if (st->done) return;
+    __shared__ double sh[RED_THREADS];
+    const float alpha = (float)st->alpha;
+    Acc2 rz, rr;
+    auto step = [&](float &xi, float &ri, float pi, float qi, float di) {
+        xi = __fmaf_rn(alpha, pi, xi);
+        ri = __fmaf_rn(-alpha, qi, ri);
+        const float zi = __fmul_rn(di, ri);
+        acc2(rz, ri, zi); acc2(rr, ri, ri);
+    };
+    const Stride4 I(n);
+    float4 *x4 = reinterpret_cast<float4 *>(x), *r4 = reinterpret_cast<float4 *>(r);
+    const float4 *p4 = reinterpret_cast<const float4 *>(p), *q4 = reinterpret_cast<const float4 *>(q),
+                 *d4 = reinterpret_cast<const float4 *>(dinv);
+    for (int64_t i = I.g0; i < I.n4; i += I.gs) {
+        float4 xv = x4[i], rv = r4[i];
+        const float4 pv = p4[i], qv = q4[i], dv = d4[i];
+        step(xv.x, rv.x, pv.x, qv.x, dv.x); step(xv.y, rv.y, pv.y, qv.y, dv.y);
+        step(xv.z, rv.z, pv.z, qv.z, dv.z); step(xv.w, rv.w, pv.w, qv.w, dv.w);
+        x4[i] = xv; r4[i] = rv;
+    }
+    for (int64_t i = 4 * I.n4 + I.g0; i < n; i += I.gs) step(x[i], r[i], p[i], q[i], dinv[i]);
+    double s[2] = { acc2_value(rz), acc2_value(rr) }, o[2];
+    if (last_block_sum<2>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+        st->beta = o[0] / st->rz;
+        st->rz = o[0]; st->rr = o[1];
+        st->iter += 1;
+        if (!isfinite(o[1])) st->done = CG_NAN;
+        else if (o[1] <= st->tol2) st->done = CG_CONVERGED;
+        else if (st->iter >= st->max_iter) st->done = CG_MAXIT;
+    }
+}
+
+// p = dinv r + beta p (skipped once converged).
+__global__ void k_cg_direction32(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ dinv,
+                                 int64_t n, const CgState *st)
+{
+    if (st->done) return;
+    const float beta = (float)st->beta;
+    const Stride4 I(n);
+    float4 *p4 = reinterpret_cast<float4 *>(p);
+    const float4 *r4 = reinterpret_cast<const float4 *>(r), *d4 = reinterpret_cast<const float4 *>(dinv);
+    for (int64_t i = I.g0; i < I.n4; i += I.gs) {
+        float4 pv = p4[i];
+        const float4 rv = r4[i], dv = d4[i];
+        pv.x = __fmaf_rn(beta, pv.x, __fmul_rn(dv.x, rv.x));
+        pv.y = __fmaf_rn(beta, pv.y, __fmul_rn(dv.y, rv.y));
+        pv.z = __fmaf_rn(beta, pv.z, __fmul_rn(dv.z, rv.z));
+        pv.w = __fmaf_rn(beta, pv.w, __fmul_rn(dv.w, rv.w));
+        p4[i] = pv;
+    }
+    for (int64_t i = 4 * I.n4 + I.g0; i < n; i += I.gs) p[i] = __fmaf_rn(beta, p[i], __fmul_rn(dinv[i], r[i]));
+}
+
+// y = 2^e x in FP64 (the FP32 CG solution of the unscaled system; exact)
+__global__ void k_cg_widen(double *__restrict__ y, const float *__restrict__ x, int64_t n, const CgState *st)
+{
+    const double sc = ldexp(1.0, st->scale_exp);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (double)x[i] * sc;
 }
 
 }  // namespace feod

@@ -18,6 +18,7 @@ struct CgState {
     int iter, max_iter;
     int done;
     unsigned counter;      // last-block ticket of the reductions (returns to 0 after each)
+    int scale_exp;         // FP32 CG: the system is solved for b / 2^scale_exp
     double scalar;         // result slot of plain dot products
 };
 
@@ -29,19 +30,30 @@ __global__ void k_design_factors(const GeomParams G, const double *__restrict__ 
                                  double kappa_q, double *__restrict__ kr, double *__restrict__ dkr);
 __global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *partial,
                       unsigned *counter, double *out);
-__global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, double *__restrict__ x,
+__global__ void k_cg_init(const double *__restrict__ b, const float *__restrict__ dinv, double *__restrict__ x,
                           double *__restrict__ r, double *__restrict__ p, int64_t n, CgState *st, double rtol,
                           int max_iter, double *partial);
 __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restrict__ q, int64_t n, CgState *st,
                            double *partial);
 __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, CgState *st,
+                            const double *__restrict__ q, const float *__restrict__ dinv, int64_t n, CgState *st,
                             double *partial);
-__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
+__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const float *__restrict__ dinv,
                                int64_t n, const CgState *st);
 __global__ void k_waxpy(double *__restrict__ y, const double *__restrict__ a, double alpha,
                         const double *__restrict__ b, int64_t n);
 __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, double alpha, int64_t n);
-__global__ void k_reciprocal(double *__restrict__ y, const double *__restrict__ x, int64_t n);
+__global__ void k_reciprocal(float *__restrict__ y, const double *__restrict__ x, int64_t n);
+__global__ void k_cg_init32(const double *__restrict__ b, const float *__restrict__ dinv, float *__restrict__ x,
+                            float *__restrict__ r, float *__restrict__ p, int64_t n, CgState *st, const double *bb,
+                            double rtol, int max_iter, double *partial);
+__global__ void k_cg_alpha32(const float *__restrict__ p, const float *__restrict__ q, int64_t n, CgState *st,
+                             double *partial);
+__global__ void k_cg_update32(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ p,
+                              const float *__restrict__ q, const float *__restrict__ dinv, int64_t n, CgState *st,
+                              double *partial);
+__global__ void k_cg_direction32(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ dinv,
+                                 int64_t n, const CgState *st);
+__global__ void k_cg_widen(double *__restrict__ y, const float *__restrict__ x, int64_t n, const CgState *st);
 
 }  // namespace feod

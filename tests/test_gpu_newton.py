@@ -124,3 +124,27 @@ def test_compliance_gradient_against_fd():
         fd = (cp - cm).item() / (2 * h)
         assert abs(fd - torch.dot(g, d).item()) <= 1e-6 * abs(torch.dot(g, d).item())
     op.close()
+
+
+def test_cg_solve_fp32_accuracy_and_scaling():
+    """FP32 CG: the FP64 operator confirms its solution's residual, and scaling b by 2^s gives
+    bitwise 2^s x, also where b's entries lie far outside the FP32 range (the solver works on
+    b divided by a power of two near its RMS)."""
+    import torch
+    w = I.Workload("3d_small", 3, 5, 2)
+    op, P, u0, ud = _setup(w)
+    op.linearize(ud)
+    F = op.load_vector()
+    b = -op.residual(ud)
+    for rhs in (F, b):
+        x, it = op.cg_solve(rhs, rtol=1e-6, precision=32)
+        assert it > 0
+        res = rhs - op.jacobian_action(x)
+        assert torch.linalg.norm(res) <= 1e-5 * torch.linalg.norm(rhs)
+        x64, _ = op.cg_solve(rhs, rtol=1e-12, precision=64)
+        assert torch.linalg.norm(x - x64) <= 5e-4 * torch.linalg.norm(x64)
+        for s in (-140, 150):
+            xs, its = op.cg_solve(rhs * 2.0 ** s, rtol=1e-6, precision=32)
+            assert its == it
+            assert torch.equal(xs, x * 2.0 ** s)
+    op.close()
