@@ -253,7 +253,9 @@ def run_gpu(args) -> dict | None:
     # ---- Newton solves: FP64 and mixed precision to 1e-8 ----
     newton = {}
     if not args.no_newton:
-        for name, prec in (("mixed", 32), ("fp64", 64)):
+        # mixed: FP32 J v inside an FP64 CG; mixed_fp32_cg: FP32 J v and FP32 CG vectors with
+        # compensated inner products; fp64: everything FP64
+        for name, prec in (("mixed", -32), ("mixed_fp32_cg", 32), ("fp64", 64)):
             u = u0.clone()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -265,8 +267,9 @@ def run_gpu(args) -> dict | None:
                             "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
                             "rel_residual": rep["rel"], "cg_time_s": round(rep["cg_ms"] / 1e3, 4),
                             "kernel_launches": rep["launches"]}
-        if "fp64" in newton and "mixed" in newton:
-            newton["speedup_mixed_vs_fp64"] = round(newton["fp64"]["time_s"] / newton["mixed"]["time_s"], 3)
+        for name in ("mixed", "mixed_fp32_cg"):
+            if "fp64" in newton and name in newton:
+                newton[f"speedup_{name}_vs_fp64"] = round(newton["fp64"]["time_s"] / newton[name]["time_s"], 3)
 
     if rank != 0:
         op.close()
@@ -314,6 +317,155 @@ def run_gpu(args) -> dict | None:
     op.close()
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# measurement suites beside the headline: the order sweep and the design-sensitivity case
+# ------------------------------------------------------------------------------------------------
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 rate of the GB300 (no measured FP64 peak is recorded)
+
+
+def jv_algorithmic_flops(dim: int, n_e: int, d1: int, q1: int) -> float:
+    """Flops of one partially assembled J v: per element, interpolation plus collocated gradient
+    in both directions (4 d D1^(d+1) multiply-adds) and the symmetric d x d matvec per point."""
+    return 2.0 * n_e * (4 * dim * d1 ** (dim + 1) + dim * dim * q1 ** dim)
+
+
+def _event_time(fn, steps: int, warmup: int) -> float:
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / steps
+
+
+def _newton_modes(op, u0, max_newton: int) -> dict:
+    import torch
+    out = {}
+    for name, prec in (("mixed", -32), ("mixed_fp32_cg", 32), ("fp64", 64)):
+        u = u0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = op.newton_solve(u, rtol=1e-8, inner_precision=prec, max_newton=max_newton, raise_on_error=False)
+        torch.cuda.synchronize()
+        out[name] = {"time_s": round(time.perf_counter() - t0, 4), "status": rep["status"],
+                     "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
+                     "rel_residual": rep["rel"]}
+    for name in ("mixed", "mixed_fp32_cg"):
+        out[f"speedup_{name}_vs_fp64"] = round(out["fp64"]["time_s"] / out[name]["time_s"], 3)
+    return out
+
+
+def run_sweep(args) -> dict:
+    """3D p=3, orders 1..6 on meshes of about 8M DOFs (k n ~ 200): FP32 / FP64 J v, FP64 residual
+    and the three Newton modes per order."""
+    import torch
+
+    from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    orders = [int(k) for k in args.orders.split(",")]
+    rows = []
+    clk = ClockSampler(0).start()
+    for k in orders:
+        w = I.sweep_workload(k)
+        V = I.lattice_vertices(3, w.n, seed=w.mesh_seed)
+        op = Operator(3, w.n, k, V, p=w.p, eps=w.eps)
+        nl, ne, nq = op.n_dofs, op.n_elements, (k + 1) ** 3
+        u0 = torch.from_numpy(I.smooth_field(3, w.n, k, seed=w.state_seed)).cuda()
+        v64 = torch.from_numpy(I.uniform_vector(nl, seed=w.dir_seed)).cuda()
+        v32 = v64.float()
+        y32, y64 = torch.empty_like(v32), torch.empty_like(v64)
+        op.linearize(u0)
+        t32 = _event_time(lambda: op.jacobian_action(v32, precision=32, out=y32), 30, 3)
+        op.prof_enable(True); op.prof_reset()
+        for _ in range(10):
+            op.jacobian_action(v32, precision=32, out=y32)
+        prof = op.prof_read(); op.prof_enable(False)
+        kn, kms = prof.get("jv_pa_f32", (1, float("nan")))
+        t_main = kms / 1e3 / max(kn, 1)
+        t64 = _event_time(lambda: op.jacobian_action(v64, precision=64, out=y64), 5, 2)
+        r = torch.empty_like(u0)
+        tres = _event_time(lambda: op.residual(u0, out=r), 3, 1)
+        b32 = jv_algorithmic_bytes(nl, ne, nq, nq, 4)
+        fl = jv_algorithmic_flops(3, ne, k + 1, k + 1)
+        row = {"order": k, "n": w.n, "n_dofs": nl, "n_elements": ne,
+               "jv_f32_gdofs": round(nl / t32 / 1e9, 3), "jv_f32_ms": round(t32 * 1e3, 4),
+               "jv_f32_main_kernel_ms": round(t_main * 1e3, 4),
+               "jv_f32_hbm_frac": round(b32 / t_main / 1e9 / peaks["hbm_gbs"], 4),
+               "jv_f64_gdofs": round(nl / t64 / 1e9, 3),
+               "jv_f64_fp64_frac": round(fl / t64 / 1e12 / FP64_PEAK_TFLOPS, 4),
+               "residual_f64_gdofs": round(nl / tres / 1e9, 3)}
+        if not args.no_newton:
+            row["newton"] = _newton_modes(op, u0, args.max_newton)
+        rows.append(row)
+        op.close()
+        del u0, v64, v32, y32, y64
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    return {"suite": "sweep", "workload": "3D p-Laplacian p=3, orders %s, k n ~ 200 (about 8M DOFs)" % args.orders,
+            "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"],
+            "fp64_peak_tflops": FP64_PEAK_TFLOPS, "fp64_peak_source": "nominal",
+            "jv_f32_hbm_frac_note": "algorithmic bytes (v, y, 6 tangent words per point, 4 B index per "
+                                    "E-vector entry) / main kernel time, fix-up excluded",
+            "clocks": clocks, "orders": rows}
+
+
+def run_design(args) -> dict:
+    """Design sensitivity on 48^3 order 2: kappa(rho) = 1e-3 + rho^3 times the p=3 flux; Newton,
+    the adjoint gradient of the compliance through the autograd function, and central differences
+    on 20 seeded directions."""
+    import numpy as np
+    import torch
+
+    from paper_2506_00746_gb300 import ComplianceFn, Operator
+    from paper_2506_00746_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    w = I.WORKLOADS["3d_design_k2_48"]
+    V = I.lattice_vertices(3, w.n, seed=w.mesh_seed)
+    rho0 = I.design_field(3, w.n, seed=3)
+    op = Operator(3, w.n, w.order, V, p=w.p, eps=w.eps, rho=rho0)
+    u0 = torch.from_numpy(I.smooth_field(3, w.n, w.order, seed=w.state_seed)).cuda()
+    kw = {"rtol": 1e-12, "cg_rtol": 1e-8}
+    rho = torch.from_numpy(rho0).cuda().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = ComplianceFn.apply(rho, op, u0, kw)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    c.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    g = rho.grad.detach().clone()
+    rng = np.random.default_rng(4)
+    h = 1e-5
+    errs, t_fd = [], 0.0
+    for _ in range(args.fd_dirs):
+        d = torch.from_numpy(rng.standard_normal(op.n_elements)).cuda()
+        t0 = time.perf_counter()
+        with torch.no_grad():
+            cp = ComplianceFn.apply(rho.detach() + h * d, op, u0, kw).item()
+            cm = ComplianceFn.apply(rho.detach() - h * d, op, u0, kw).item()
+        t_fd += time.perf_counter() - t0
+        fd = (cp - cm) / (2 * h)
+        gd = torch.dot(g, d).item()
+        errs.append(abs(fd - gd) / abs(gd))
+    out = {"suite": "design", "workload": "3d_design_k2_48: 48^3 hex, order 2, p=3, kappa = 1e-3 + rho^3, "
+                                          "rho seeded U[0,1] per element, compliance F^T u, FP64",
+           "n_dofs": op.n_dofs, "n_elements": op.n_elements, "compliance": c.item(),
+           "forward_newton_s": round(t_fwd, 4), "adjoint_backward_s": round(t_bwd, 4),
+           "fd_directions": args.fd_dirs, "fd_step": h, "fd_rel_err_max": max(errs),
+           "fd_rel_err_median": float(np.median(errs)), "fd_time_s": round(t_fd, 3)}
+    op.close()
     return out
 
 
@@ -398,10 +550,17 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-newton", type=int, default=50)
+    ap.add_argument("--suite", choices=["headline", "sweep", "design"], default="headline",
+                    help="headline (the benchmark line), sweep (orders 1-6) or design (adjoint case)")
+    ap.add_argument("--orders", default="1,2,3,4,5,6")
+    ap.add_argument("--fd-dirs", type=int, default=20)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.suite != "headline" and args.impl == "gpu":
+        out = run_sweep(args) if args.suite == "sweep" else run_design(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
         print(json.dumps(out), flush=True)
     import torch.distributed as dist

@@ -185,7 +185,8 @@ typedef struct {
     int max_newton;
     int max_cg;                /* per Newton step                                              */
     double cg_rtol;            /* inner CG stops when ||r_cg|| <= cg_rtol ||R(u_k)||           */
-    int inner_precision;       /* 64: FP64 CG; 32: FP32 CG (FP32 J v and vectors; mixed)       */
+    int inner_precision;       /* CG precision, as fe_jacobian_action's: 64 FP64; -32 FP32 J v
+                                  in an FP64 CG; 32 FP32 J v and FP32 CG vectors              */
     int line_search;           /* 1: backtracking on ||R||_2                                   */
     double armijo;             /* accept alpha when ||R(u+alpha d)|| <= (1-armijo alpha)||R(u)|| */
     int max_halvings;
@@ -214,19 +215,21 @@ fe_status fe_newton_default_opts(fe_newton_opts *opts);
  * overwritten with the solution.  Each step: R and J_D at u (fused, FP64 dual numbers), Jacobi-
  * preconditioned CG on J d = -R with the partially assembled J, then a backtracking line search
  * on ||R|| (R, its norm, u and the line search always FP64).  inner_precision 64: the CG runs in
- * FP64.  inner_precision 32: the CG runs on FP32 vectors with the FP32 operator, for -R scaled by
- * a power of two near its RMS (exact), with its inner products accumulated in compensated FP32
- * (Ogita-Rump-Oishi Dot2) and summed in FP64; its scalars are FP64.  All reductions run in a
- * fixed order, so results are bitwise reproducible on a given GPU model.  Runs on an internal
- * stream after synchronising `stream`; synchronous (returns after the solve).  report may be NULL. */
+ * FP64.  -32: the FP32 operator (FP32 arithmetic on the FP32 rounding of the stored tangent) is
+ * applied to FP64 CG vectors; dot products, norms and updates FP64.  32: the CG runs on FP32
+ * vectors with the FP32 operator, for -R scaled by a power of two near its RMS (exact), with its
+ * inner products accumulated in compensated FP32 (Ogita-Rump-Oishi Dot2) and summed in FP64; its
+ * scalars are FP64.  All reductions run in a fixed order, so results are bitwise reproducible on
+ * a given GPU model.  Runs on an internal stream after synchronising `stream`; synchronous
+ * (returns after the solve).  report may be NULL. */
 fe_status newton_solve(fe_ctx *ctx, double *u_inout, const fe_newton_opts *opts,
                        fe_newton_report *report, void *stream);
 
 /* fe_cg_solve: solve J x = b with the cached linearisation (e.g. the adjoint J lambda = F; J is
- * symmetric), x starting from 0, Jacobi-preconditioned CG to ||r|| <= rtol ||b||.  precision 64:
- * FP64 operator and vectors; 32: FP32 operator and vectors as in newton_solve's inner_precision
- * 32 (its attainable relative residual is about 1e-6, so a smaller rtol ends in
- * FE_ERR_NOT_CONVERGED at max_iter).  b, x: device double[N_L].  Synchronous.  iters may be NULL. */
+ * symmetric), x starting from 0, Jacobi-preconditioned CG to ||r|| <= rtol ||b||.  precision 64,
+ * -32 or 32 as newton_solve's inner_precision (with 32 the attainable relative residual is about
+ * 1e-6, so a smaller rtol ends in FE_ERR_NOT_CONVERGED at max_iter).  b, x: device double[N_L].
+ * Synchronous.  iters may be NULL. */
 fe_status fe_cg_solve(fe_ctx *ctx, const double *b, double *x, double rtol, int max_iter,
                       int precision, int *iters, void *stream);
 

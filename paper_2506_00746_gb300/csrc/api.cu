@@ -208,8 +208,8 @@ fe_status apply_jv_cached(fe_ctx *c, const void *v, void *y, int precision, cuda
 }
 
 // Enqueue `m` CG iterations (J p, alpha, update, direction); every kernel is a no-op once the
-// device flag `done` is set.  precision 64: FP64 operator and vectors; 32: FP32 operator and
-// vectors (CG scalars and inner-product sums in FP64).
+// device flag `done` is set.  precision 64: FP64 operator and vectors; -32: FP32 operator, FP64
+// vectors; 32: FP32 operator and vectors (CG scalars and inner-product sums in FP64).
 void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
 {
     CgState *s = cg_state(c);
@@ -217,8 +217,9 @@ void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
     c->op.skip = &s->done;
     c->fix.skip = &s->done;
     for (int i = 0; i < m; ++i) {
-        if (precision == 64) {
-            c->ops->jv_pa_64(c, c->w_cp, c->w_cq, st);
+        if (precision != 32) {
+            if (precision == 64) c->ops->jv_pa_64(c, c->w_cp, c->w_cq, st);
+            else c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
             { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
             { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv, n, s, c->w_partial); }
             { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cp, c->w_cr, c->w_dinv, n, s); }
@@ -239,7 +240,7 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
 {
     cudaStream_t st = c->own_stream;
     CgState *s = cg_state(c);
-    if (precision == 64) {
+    if (precision != 32) {
         LaunchScope ls(c, "cg_init", st);
         k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->nl, s, rtol,
                                                       max_iter, c->w_partial);
@@ -256,7 +257,7 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
     }
     CKLAUNCH();
     if (batch < 1) batch = 1;
-    const int gi = precision == 64 ? 0 : 1;
+    const int gi = precision == 64 ? 0 : precision == -32 ? 1 : 2;
     if (use_graph && (c->cg_exec[gi] == nullptr || c->cg_batch[gi] != batch)) {
         if (c->cg_exec[gi]) { cudaGraphExecDestroy(c->cg_exec[gi]); c->cg_exec[gi] = nullptr; }
         const bool prof = c->prof;
@@ -288,7 +289,7 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
         CK(cudaStreamSynchronize(st));
         if (h->done) break;
     }
-    if (precision != 64) {
+    if (precision == 32) {
         // the FP32 solution, unscaled, into the FP64 solution vector
         LaunchScope ls(c, "cg_widen", st);
         k_cg_widen<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cx, c->w_fx, c->nl, s);
@@ -742,8 +743,9 @@ extern "C" fe_status fe_cg_solve(fe_ctx *c, const double *b, double *x, double r
 {
     if (!c) return FE_ERR_ARG;
     if (!b || !x || b == x) return fail(c, FE_ERR_ARG, "fe_cg_solve: null or aliased vectors");
-    if (precision != 64 && precision != 32) return fail(c, FE_ERR_ARG, "precision must be 64 or 32");
-    if ((precision == 64 && !c->lin64) || (precision == 32 && !c->lin32) || !c->have_diag)
+    if (precision != 64 && precision != 32 && precision != -32)
+        return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
+    if ((precision == 64 && !c->lin64) || (precision != 64 && !c->lin32) || !c->have_diag)
         return fail(c, FE_ERR_STATE, "no linearisation cached (call fe_linearize)");
     fe_status s = ensure_work(c);
     if (s != FE_OK) return s;
@@ -789,11 +791,11 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
     if (!u) return fail(c, FE_ERR_ARG, "newton_solve: null u");
     fe_newton_opts o;
     if (opts_in) o = *opts_in; else fe_newton_default_opts(&o);
-    if (o.inner_precision != 64 && o.inner_precision != 32)
-        return fail(c, FE_ERR_ARG, "inner_precision must be 64 or 32");
+    if (o.inner_precision != 64 && o.inner_precision != 32 && o.inner_precision != -32)
+        return fail(c, FE_ERR_ARG, "inner_precision must be 64, 32 or -32");
     fe_newton_report R;
     std::memset(&R, 0, sizeof R);
-    const bool mixed = o.inner_precision == 32;
+    const bool mixed = o.inner_precision != 64;
     fe_status s = ensure_work(c);
     if (s == FE_OK) s = ensure_tangent(c, !mixed, mixed);
     if (s != FE_OK) return s;
@@ -804,7 +806,7 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
     double cg_ms = 0.0;
     double *T64 = mixed ? nullptr : c->d_T64;
     float *T32 = mixed ? c->d_T32 : nullptr;
-    const int jprec = mixed ? 32 : 64;
+    const int jprec = o.inner_precision;
 
     // R and J_D at u (fused)
     c->ops->residual(c, u, c->w_r, T64, T32, st);

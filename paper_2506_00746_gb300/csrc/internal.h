@@ -172,10 +172,11 @@ struct fe_ctx {
     double *w_partial = nullptr;  // reduction partials
     void *h_state = nullptr;      // pinned host mirror
     cudaStream_t own_stream = nullptr;
-    // captured CG batches, [0] FP64 operator and vectors, [1] FP32 operator and vectors
-    cudaGraphExec_t cg_exec[2] = { nullptr, nullptr };
-    int cg_batch[2] = { 0, 0 };
-    int64_t cg_launches[2] = { 0, 0 };
+    // captured CG batches: [0] FP64 operator and vectors, [1] FP32 operator with FP64 vectors,
+    // [2] FP32 operator and vectors
+    cudaGraphExec_t cg_exec[3] = { nullptr, nullptr, nullptr };
+    int cg_batch[3] = { 0, 0, 0 };
+    int64_t cg_launches[3] = { 0, 0, 0 };
 
     feod::OpParams op{};
     feod::FixParams fix{};

@@ -83,3 +83,36 @@ def test_config2_sampled_parity():
     b = torch.dot(vm, op.jacobian_action(w2, precision=64)).item()
     assert abs(a - b) <= 1e-12 * abs(a)
     op.close()
+
+
+def test_design_fullsize_against_oracle():
+    """The design case at full size (48^3 hexes, order 2, kappa(rho) = 1e-3 + rho^3, p = 3): the
+    oracle evaluates the GPU's Newton solution (its own residual), the GPU's adjoint solution
+    (its own J(u) lambda - F) and the GPU's gradient (its element-local adjoint formula at the
+    GPU's u and lambda)."""
+    import torch
+    from paper_2506_00746_gb300 import Operator
+    w = I.WORKLOADS["3d_design_k2_48"]
+    V = I.lattice_vertices(3, w.n, seed=w.mesh_seed)
+    rho = I.design_field(3, w.n, seed=3)
+    op = Operator(3, w.n, w.order, V, p=w.p, rho=rho)
+    assert op.n_dofs == 912_673
+    u0 = I.smooth_field(3, w.n, w.order, seed=w.state_seed)
+    ud = torch.from_numpy(u0).cuda()
+    rep = op.newton_solve(ud, rtol=1e-10, cg_rtol=1e-6)
+    assert rep["rel"] <= 1e-10
+    op.linearize(ud)
+    F = op.load_vector()
+    lam, _ = op.cg_solve(F, rtol=1e-12)
+    g = op.adjoint_vjp(ud, lam).cpu().numpy()
+    u, lamh, Fh = ud.cpu().numpy(), lam.cpu().numpy(), F.cpu().numpy()
+    P = O.Problem(3, w.n, w.order, V, p=w.p, rho=rho)
+    nrm = np.linalg.norm
+    assert nrm(O.residual(P, u)) <= 1e-10 * nrm(O.residual(P, u0)) * 1.01
+    F_ref = O.load(P)
+    F_ref[O.essential(P)] = 0.0          # the library's load vector is zero on essential DOFs
+    assert nrm(Fh - F_ref) <= 1e-12 * nrm(F_ref)
+    assert nrm(O.jv(P, u, lamh) - F_ref) <= 1e-10 * nrm(F_ref)
+    g_ref = O.adjoint_grad(P, u, lamh)
+    assert nrm(g - g_ref) <= 1e-12 * nrm(g_ref)
+    op.close()

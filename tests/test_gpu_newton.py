@@ -21,7 +21,7 @@ def _setup(w: I.Workload):
     return op, P, u0, torch.from_numpy(u0).cuda()
 
 
-@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("precision", [64, -32, 32])
 def test_newton_2d_config(precision):
     """2D p=3, 16x16 quads, order 2: Newton-CG to 1e-8 in FP64 and mixed precision."""
     w = I.WORKLOADS["2d_p3_k2_16x16"]
@@ -37,7 +37,7 @@ def test_newton_2d_config(precision):
     op.close()
 
 
-@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("precision", [64, -32, 32])
 def test_newton_tight_matches_oracle(precision):
     w = I.Workload("3d_small", 3, 4, 2)
     op, P, u0, ud = _setup(w)
@@ -54,11 +54,12 @@ def test_newton_graph_and_plain_launches_agree():
     import torch
     w = I.Workload("3d_small", 3, 3, 3)
     op, P, u0, ud = _setup(w)
-    a, b = ud.clone(), ud.clone()
-    ra = op.newton_solve(a, inner_precision=32, use_graph=True)
-    rb = op.newton_solve(b, inner_precision=32, use_graph=False, cg_batch=5)
-    assert torch.equal(a, b)
-    assert ra["cg_hist"] == rb["cg_hist"]
+    for prec in (32, -32):
+        a, b = ud.clone(), ud.clone()
+        ra = op.newton_solve(a, inner_precision=prec, use_graph=True)
+        rb = op.newton_solve(b, inner_precision=prec, use_graph=False, cg_batch=5)
+        assert torch.equal(a, b)
+        assert ra["cg_hist"] == rb["cg_hist"]
     op.close()
 
 
