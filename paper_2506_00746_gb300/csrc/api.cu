@@ -448,6 +448,9 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
             c->b64.B[i] = B; c->b64.G[i] = G; c->b64.B2[i] = B * B; c->b64.G2[i] = G * G; c->b64.BG[i] = B * G;
             c->b32.B[i] = (float)B; c->b32.G[i] = (float)G; c->b32.B2[i] = (float)(B * B);
             c->b32.G2[i] = (float)(G * G); c->b32.BG[i] = (float)(B * G);
+            c->p32.BG[i] = make_float2((float)B, (float)G);
+            c->p32.GB[i] = make_float2((float)G, (float)B);
+            c->p32.BB[i] = make_float2((float)B, (float)B);
         }
     c->gp.dim = dim; c->gp.d1 = c->d1; c->gp.q1 = c->q1; c->gp.n = n; c->gp.T = T; c->gp.nt = c->nt;
     c->gp.nepad = c->nepad; c->gp.f_kind = prob->f_kind; c->gp.f_const = prob->f_const; c->gp.p = prob->p;

@@ -995,11 +995,18 @@ struct Ops {
             const int grid = c->pipe_grid[variant<TC, TIO>()];
             if (grid > 0) {
                 constexpr int TT = max_tile(3, D1 - 1);
-                const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32, c->Spad);
                 {
                     LaunchScope ls(c, name, st);
-                    k_jv_tile<D1, TT, TC, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(
-                        c->op, *bs, Tq, v, y, reinterpret_cast<TC *>(c->d_halo));
+                    if constexpr (sizeof(TC) == 4) {
+                        const size_t tsm = tile2_smem_bytes<D1, TT, TIO>(c->tqs32);
+                        k_jv_tile2<D1, TT, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                            c->op, c->p32, reinterpret_cast<const float *>(Tq), v, y,
+                            reinterpret_cast<float *>(c->d_halo));
+                    } else {
+                        const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
+                        k_jv_tile<D1, TT, TC, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                            c->op, *bs, Tq, v, y, reinterpret_cast<TC *>(c->d_halo));
+                    }
                 }
                 fixup<TC, TIO>(c, y, st);
                 return;
@@ -1026,17 +1033,25 @@ struct Ops {
         if constexpr (DIM == 3) {
             constexpr int TT = max_tile(3, D1 - 1);
             if (c->no_pipeline || c->T != TT) return cudaSuccess;
-            const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(sizeof(TC) == 8 ? c->tqs64 : c->tqs32, c->Spad);
+            // FP32: the packed kernel k_jv_tile2; FP64: k_jv_tile
+            const void *kern;
+            size_t tsm;
+            if constexpr (sizeof(TC) == 4) {
+                kern = reinterpret_cast<const void *>(k_jv_tile2<D1, TT, TIO>);
+                tsm = tile2_smem_bytes<D1, TT, TIO>(c->tqs32);
+            } else {
+                kern = reinterpret_cast<const void *>(k_jv_tile<D1, TT, TC, TIO>);
+                tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
+            }
             if (tsm > (size_t)c->smem_optin) return cudaSuccess;
-            cudaError_t e = raise_smem(k_jv_tile<D1, TT, TC, TIO>, tsm);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
             if (e != cudaSuccess) return e;
             cudaFuncAttributes fa;
-            e = cudaFuncGetAttributes(&fa, k_jv_tile<D1, TT, TC, TIO>);
+            e = cudaFuncGetAttributes(&fa, kern);
             if (e != cudaSuccess) return e;
             if (fa.maxThreadsPerBlock < TileShape<D1, TT>::THREADS) return cudaSuccess;
             int per_sm = 0;       // the launch must fit at least one CTA per SM
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jv_tile<D1, TT, TC, TIO>,
-                                                              TileShape<D1, TT>::THREADS, tsm);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TileShape<D1, TT>::THREADS, tsm);
             if (e != cudaSuccess) return e;
             if (per_sm < 1 || c->ntiles > 0x7fffffff) return cudaSuccess;
             c->pipe_grid[variant<TC, TIO>()] = (int)c->ntiles;     // one CTA per tile

@@ -47,6 +47,14 @@ struct BasisT {
     T BG[MAXQ * MAXQ];   // B*G
 };
 
+// FP32 1D basis tables as pairs, for packed (two-lane) FP32 multiply-adds: BG = (B, G),
+// GB = (G, B), BB = (B, B), row-major [q][a].
+struct BasisPairs {
+    float2 BG[MAXQ * MAXQ];
+    float2 GB[MAXQ * MAXQ];
+    float2 BB[MAXQ * MAXQ];
+};
+
 // Pointwise law kinds (uniform for a launch): kappa(base) = base^a with a = (p-2)/2.
 enum LawKind : int { LAW_GENERIC = 0, LAW_P2 = 1, LAW_P3 = 2, LAW_P4 = 3 };
 
@@ -182,6 +190,7 @@ struct fe_ctx {
     feod::FixParams fix{};
     feod::BasisT<double> b64{};
     feod::BasisT<float> b32{};
+    feod::BasisPairs p32{};
     feod::GeomParams gp{};
     const feod::OpTable *ops = nullptr;
 

@@ -355,4 +355,303 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     tile_stages<D1, TT, TC, TIO>(P, Bs, t, Tb, Vs, codes, hd, AE, Cb, SX, SY, SZ, v, y, halo, tid);
 }
 
+// ------------------------------------------------------------------------------------------------
+// FP32 variant with packed two-lane arithmetic
+// ------------------------------------------------------------------------------------------------
+// The same stages, with the contraction arrays carried as pairs so that one packed FP32
+// multiply-add (FFMA2) and one 64-bit shared-memory access serve two of them:
+//   after z   : (B_z v, G_z v)                            pair array A2
+//   after y   : c00 = B_y B_z v scalar (C1), (G_y B_z v, B_y G_z v) pair (C2)
+//   x         : gradient (G c00 | B (c01, c10)), D, transpose into d00 (C1) and (d01, d10) (C2)
+//   after y^T : (E0, E1) pair (A2 again), E0 = B^T d00 + G^T d01, E1 = B^T d10
+//   z^T       : (B^T E0, G^T E1) pair, summed at the end
+// Pair arrays use a y-slot stride congruent to SE mod 16, so that every half-warp's 64-bit access
+// touches 16 distinct bank pairs; the x stage's accesses have lane stride SE (odd) and are
+// conflict-free in both widths.
+template <int D1, int TT>
+struct TileShape2 : TileShape<D1, TT> {
+    using B = TileShape<D1, TT>;
+    static constexpr int SA2 = B::SE * B::QT + (((B::SE - B::SE * B::QT) % 16) + 16) % 16;
+    static constexpr int NA2 = SA2 * B::SE;
+};
+
+template <int D1, int TT, typename TIO>
+__host__ __device__ inline size_t tile2_smem_bytes(int64_t tqs)
+{
+    using TS = TileShape2<D1, TT>;
+    return 64 + pad16((size_t)tqs * 4) + 2 * pad16(TS::NS3 * 4) + pad16(TS::NS3 * sizeof(TIO)) +
+           pad16((size_t)TS::NA2 * 8) + pad16((size_t)TS::NC * 4) + pad16((size_t)TS::NC * 8) +
+           pad16((size_t)TS::NSX * 4) + pad16((size_t)TS::NSX * 8) + pad16((size_t)TS::NSY * 8) +
+           pad16((size_t)TS::NSZ * 4);
+}
+
+// store_hd() runs after the z stage: it stores the halo positions that the prologue loaded into
+// registers (their latency overlaps the z stage; they are read only by the writes).
+// tangent_ready() runs in every thread before the x stage (the first reader of Tb) and returns
+// false, uniformly, to abandon the tile.
+template <int D1, int TT, typename TIO, typename StoreHd, typename Ready>
+__device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *Tb, const TIO *Vs,
+                                             const uint32_t *codes, const uint32_t *hd, float2 *A2, float *C1,
+                                             float2 *C2, float *SX1, float2 *SX2, float2 *SY2, float *SZ1,
+                                             const TIO *__restrict__ v, TIO *__restrict__ y,
+                                             float *__restrict__ halo, int tid, StoreHd store_hd,
+                                             Ready tangent_ready)
+{
+    using TS = TileShape2<D1, TT>;
+    constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT;
+    constexpr int SA2 = TS::SA2, NLP = TS::NLP;
+    const int L = tid % NLP, h = tid / NLP;
+
+    // z: segment h of line (sx, sy): (B v, G v) at Q1 points
+    if (L < SE * SE) {
+        const int sx = L % SE, sy = L / SE;
+        float in[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) in[a] = (float)Vs[((K * h + a) * SE + sy) * SE + sx];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) acc = __ffma2_rn(Pr.BG[q * D1 + a], make_float2(in[a], in[a]), acc);
+            A2[sx + SE * (Q1 * h + q) + SA2 * sy] = acc;
+        }
+    }
+    store_hd();
+    __syncthreads();
+    // y: segment h of line (sx, qz)
+    if (L < SE * QT) {
+        const int sx = L % SE, qz = L / SE;
+        float2 a2[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) a2[a] = A2[sx + SE * qz + SA2 * (K * h + a)];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            float c00 = 0.f;
+            float2 cp = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                c00 = fmaf(Pr.BG[q * D1 + a].x, a2[a].x, c00);
+                cp = __ffma2_rn(Pr.GB[q * D1 + a], a2[a], cp);
+            }
+            const int o = sx + SE * qz + SE * QT * (Q1 * h + q);
+            C1[o] = c00;
+            C2[o] = cp;
+        }
+    }
+    __syncthreads();
+    // x: segment h of line (qy, qz): gradient, D, x transpose
+    if (!tangent_ready()) return false;
+    float d00[D1];
+    float2 dp[D1];
+    const bool actx = L < QT * QT;
+    const int xqz = L % QT, xqy = L / QT;
+    const int xo = SE * xqz + SE * QT * xqy + K * h;
+    if (actx) {
+        float c00[D1];
+        float2 cp[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) {
+            c00[a] = C1[xo + a]; cp[a] = C2[xo + a];
+            d00[a] = 0.f; dp[a] = make_float2(0.f, 0.f);
+        }
+        const float *Tl = Tb + Q1 * (xqz + QT * (xqy + QT * h));
+        float txx[Q1], tyy[Q1], tzz[Q1], txy[Q1], txz[Q1], tyz[Q1];
+        lds_run<Q1, float>(Tl, txx);
+        lds_run<Q1, float>(Tl + NQT, tyy);
+        lds_run<Q1, float>(Tl + 2 * NQT, tzz);
+        lds_run<Q1, float>(Tl + 3 * NQT, txy);
+        lds_run<Q1, float>(Tl + 4 * NQT, txz);
+        lds_run<Q1, float>(Tl + 5 * NQT, tyz);
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            float gx = 0.f;
+            float2 gyz = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                gx = fmaf(Pr.GB[q * D1 + a].x, c00[a], gx);
+                gyz = __ffma2_rn(Pr.BB[q * D1 + a], cp[a], gyz);
+            }
+            const float fx = txx[q] * gx + txy[q] * gyz.x + txz[q] * gyz.y;
+            float2 fyz = __fmul2_rn(make_float2(txy[q], txz[q]), make_float2(gx, gx));
+            fyz = __ffma2_rn(make_float2(tyy[q], tyz[q]), make_float2(gyz.x, gyz.x), fyz);
+            fyz = __ffma2_rn(make_float2(tyz[q], tzz[q]), make_float2(gyz.y, gyz.y), fyz);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                d00[a] = fmaf(Pr.GB[q * D1 + a].x, fx, d00[a]);
+                dp[a] = __ffma2_rn(Pr.BB[q * D1 + a], fyz, dp[a]);
+            }
+        }
+    }
+    __syncthreads();       // every segment has read its c values before any is overwritten
+    if (actx) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) { C1[xo + a] = d00[a]; C2[xo + a] = dp[a]; }
+        if (h == TT - 1) {
+            C1[xo + K] = d00[K]; C2[xo + K] = dp[K];
+        } else {
+            const int so = h * QT * QT + L;
+            SX1[so] = d00[K]; SX2[so] = dp[K];
+        }
+    }
+    __syncthreads();
+    // y transpose: segment h of line (sx, qz)
+    if (L < SE * QT) {
+        const int sx = L % SE, qz = L / SE;
+        const bool xseam = (sx % K == 0) && sx > 0 && sx < SE - 1;
+        float e00[Q1];
+        float2 ep[Q1];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            const int qy = Q1 * h + q;
+            const int o = sx + SE * qz + SE * QT * qy;
+            e00[q] = C1[o]; ep[q] = C2[o];
+            if (xseam) {
+                const int so = (sx / K - 1) * QT * QT + qz + QT * qy;
+                e00[q] = SX1[so] + e00[q];
+                ep[q] = __fadd2_rn(SX2[so], ep[q]);
+            }
+        }
+        float2 E[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) E[a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < Q1; ++q)
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                E[a] = __ffma2_rn(Pr.GB[q * D1 + a], ep[q], E[a]);
+                E[a].x = fmaf(Pr.BG[q * D1 + a].x, e00[q], E[a].x);
+            }
+#pragma unroll
+        for (int a = 0; a < K; ++a) A2[sx + SE * qz + SA2 * (K * h + a)] = E[a];
+        if (h == TT - 1) A2[sx + SE * qz + SA2 * (SE - 1)] = E[K];
+        else SY2[h * QT * SE + L] = E[K];
+    }
+    __syncthreads();
+    // z transpose: segment h of line (sx, sy); P^T and the writes
+    float out[D1];
+    const bool actz = L < SE * SE;
+    const int zx = L % SE, zy = L / SE;
+    auto write_slot = [&](int sz, float val) {
+        const int s = (sz * SE + zy) * SE + zx;
+        const uint32_t code = codes[s];
+        if (code == SLOT_INVALID) return;
+        const uint32_t g = code & SLOT_GMASK;
+        if (code & SLOT_HALO) {
+            if (!(code & SLOT_ESS)) halo[hd[s]] = val;
+        } else if (code & SLOT_ESS) {
+            y[g] = v[g];
+        } else {
+            y[g] = (TIO)val;
+        }
+    };
+    if (actz) {
+        const bool yseam = (zy % K == 0) && zy > 0 && zy < SE - 1;
+        float2 z2[Q1];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            const int qz = Q1 * h + q;
+            z2[q] = A2[zx + SE * qz + SA2 * zy];
+            if (yseam) z2[q] = __fadd2_rn(SY2[(zy / K - 1) * QT * SE + zx + SE * qz], z2[q]);
+        }
+        float2 o2[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) o2[a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < Q1; ++q)
+#pragma unroll
+            for (int a = 0; a < D1; ++a) o2[a] = __ffma2_rn(Pr.BG[q * D1 + a], z2[q], o2[a]);
+#pragma unroll
+        for (int a = 0; a < D1; ++a) out[a] = o2[a].x + o2[a].y;
+#pragma unroll
+        for (int a = 1; a < K; ++a) write_slot(K * h + a, out[a]);
+        if (h == 0) write_slot(0, out[0]);
+        if (h == TT - 1) write_slot(SE - 1, out[K]);
+        else SZ1[h * SE * SE + L] = out[K];
+    }
+    __syncthreads();
+    if (actz && h > 0) write_slot(K * h, SZ1[(h - 1) * SE * SE + L] + out[0]);
+    return true;
+}
+
+// One CTA per tile (FP32 compute; TIO float or double), as k_jv_tile.
+template <int D1, int TT, typename TIO>
+__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
+    k_jv_tile2(const __grid_constant__ OpParams P, const __grid_constant__ BasisPairs Pr,
+               const float *__restrict__ Tq, const TIO *__restrict__ v, TIO *__restrict__ y,
+               float *__restrict__ halo)
+{
+    using TS = TileShape2<D1, TT>;
+    constexpr int NS3 = TS::NS3, NTH = TS::THREADS;
+    if (P.skip && *P.skip) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int64_t t = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int64_t tqs = tq_stride<float>(P);
+    const uint32_t tq_bytes = (uint32_t)(tqs * sizeof(float));
+
+    unsigned char *p = smem;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(p);    p += 64;
+    float *Tb = reinterpret_cast<float *>(p);           p += pad16(tq_bytes);
+    uint32_t *codes = reinterpret_cast<uint32_t *>(p);  p += pad16(NS3 * 4);
+    uint32_t *hd = reinterpret_cast<uint32_t *>(p);     p += pad16(NS3 * 4);
+    TIO *Vs = reinterpret_cast<TIO *>(p);               p += pad16(NS3 * sizeof(TIO));
+    float2 *A2 = reinterpret_cast<float2 *>(p);         p += pad16((size_t)TS::NA2 * 8);
+    float *C1 = reinterpret_cast<float *>(p);           p += pad16((size_t)TS::NC * 4);
+    float2 *C2 = reinterpret_cast<float2 *>(p);         p += pad16((size_t)TS::NC * 8);
+    float *SX1 = reinterpret_cast<float *>(p);          p += pad16((size_t)TS::NSX * 4);
+    float2 *SX2 = reinterpret_cast<float2 *>(p);        p += pad16((size_t)TS::NSX * 8);
+    float2 *SY2 = reinterpret_cast<float2 *>(p);        p += pad16((size_t)TS::NSY * 8);
+    float *SZ1 = reinterpret_cast<float *>(p);
+
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(mbar, tq_bytes);
+        tma_load_1d(Tb, Tq + t * tqs, tq_bytes, mbar);
+    }
+    // input gather: slot codes, then (one batch) the input values and, for halo slots, their
+    // halo-array positions, which reach shared memory after the z stage
+    constexpr int NPER = (NS3 + NTH - 1) / NTH;
+    uint32_t hr[NPER];
+    {
+        const uint32_t *sl = P.slot + t * P.Spad;
+        const uint32_t *hs = P.hdst + t * P.Spad;
+        uint32_t cr[NPER];
+#pragma unroll
+        for (int i = 0; i < NPER; ++i) {
+            const int s = tid + i * NTH;
+            cr[i] = s < NS3 ? sl[s] : SLOT_INVALID;
+        }
+        TIO vr[NPER];
+#pragma unroll
+        for (int i = 0; i < NPER; ++i) {
+            vr[i] = (cr[i] & SLOT_ESS) ? TIO(0) : v[cr[i] & SLOT_GMASK];
+            hr[i] = (cr[i] & SLOT_HALO) && !(cr[i] & SLOT_ESS) ? hs[tid + i * NTH] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < NPER; ++i) {
+            const int s = tid + i * NTH;
+            if (s < NS3) { codes[s] = cr[i]; Vs[s] = vr[i]; }
+        }
+    }
+    // makes thread 0's mbarrier initialisation and the gathered block visible to all threads;
+    // the tangent block is waited for (bounded) only before the x stage, its first reader
+    __syncthreads();
+    const bool ok = tile_stages2<D1, TT, TIO>(
+        Pr, Tb, Vs, codes, hd, A2, C1, C2, SX1, SX2, SY2, SZ1, v, y, halo, tid,
+        [&]() {
+#pragma unroll
+            for (int i = 0; i < NPER; ++i) {
+                const int s = tid + i * NTH;
+                if (s < NS3) hd[s] = hr[i];
+            }
+        },
+        [&]() { return !__syncthreads_or(!mbar_wait_bounded(mbar, 0)); });
+    if (!ok && tid == 0) {
+        // the tangent block did not land within the bound: report, let the copy finish
+        atomicExch(P.err, 3);
+        mbar_wait_bounded(mbar, 0);
+    }
+}
+
 }  // namespace feod
