@@ -469,6 +469,91 @@ def run_design(args) -> dict:
     return out
 
 
+def run_batched(args) -> dict:
+    """64 independent instances (p ~ U[2.5,4], n in [8,40], orders 1-4, seed 5): the batched FP32
+    J v in one persistent launch against the same instances' single-instance actions one after
+    another, and the lock-step batched Newton (FP32 CG, FP64 outer) against per-instance solves."""
+    import torch
+
+    from paper_2506_00746_gb300 import Batch, Operator
+    from paper_2506_00746_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    ws = I.batched_instances(64, seed=5)
+    inst = [{"vertices": I.lattice_vertices(3, w.n, seed=w.mesh_seed), "n": w.n, "order": w.order, "p": w.p}
+            for w in ws]
+    cache = os.path.join(ROOT, "paper_2506_00746_gb300", "_build", "tune_cache.json")
+    t0 = time.perf_counter()
+    B = Batch(inst, tune=True, tune_cache=cache)
+    t_create = time.perf_counter() - t0
+    us = [I.smooth_field(3, w.n, w.order, seed=w.state_seed) for w in ws]
+    u0 = B.concat(us)
+    B.linearize(u0)
+    v = B.concat([I.uniform_vector(n, seed=w.dir_seed) for n, w in zip(B.n_dofs, ws)], torch.float32)
+    y = torch.empty_like(v)
+    total_dofs = sum(B.n_dofs)
+    bytes_alg = sum(jv_algorithmic_bytes(n, w.n ** 3, (w.order + 1) ** 3, (w.order + 1) ** 3, 4)
+                    for n, w in zip(B.n_dofs, ws))
+    clk = ClockSampler(0).start()
+    l0 = B.shape()["launches"]
+    t_b = _event_time(lambda: B.jacobian_action(v, out=y), args.steps, args.warmup)
+    launches = (B.shape()["launches"] - l0) / (args.steps + args.warmup)
+    # the same instances one after another through their own single-instance operators
+    ops = [Operator(3, d["n"], d["order"], d["vertices"], p=d["p"]) for d in inst]
+    vs, ys = [], []
+    for i, op in enumerate(ops):
+        op.linearize(torch.from_numpy(us[i]).cuda())
+        vs.append(B.split(v)[i].clone())
+        ys.append(torch.empty_like(vs[-1]))
+
+    def seq():
+        for op, vi, yi in zip(ops, vs, ys):
+            op.jacobian_action(vi, precision=32, out=yi)
+    t_s = _event_time(seq, max(5, args.steps // 4), 3)
+    clocks = clk.stop()
+    out = {"suite": "batched", "workload": "64 instances, p ~ U[2.5,4], n in [8,40], orders 1-4 (seed 5), "
+                                          "%d DOFs in total" % total_dofs,
+           "n_instances": len(ws), "n_dofs_total": total_dofs,
+           "orders": {k: sum(w.order == k for w in ws) for k in (1, 2, 3, 4)},
+           "tiles_by_order": {k: next((t for t, w in zip(B.tiles, ws) if w.order == k), None) for k in (1, 2, 3, 4)},
+           "launch": B.shape(), "create_and_tune_s": round(t_create, 3),
+           "batched_jv_ms": round(t_b * 1e3, 4), "batched_jv_gdofs": round(total_dofs / t_b / 1e9, 3),
+           "batched_jv_launches_per_step": launches,
+           "batched_jv_hbm_frac": round(bytes_alg / t_b / 1e9 / peaks["hbm_gbs"], 4),
+           "sequential_jv_ms": round(t_s * 1e3, 4), "sequential_jv_gdofs": round(total_dofs / t_s / 1e9, 3),
+           "sequential_jv_launches_per_step": 2 * len(ws),
+           "batching_speedup_jv": round(t_s / t_b, 3), "clocks": clocks,
+           "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"]}
+    if not args.no_newton:
+        u = u0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps, tot = B.newton_solve(u, rtol=1e-8, raise_on_error=False)
+        torch.cuda.synchronize()
+        t_bn = time.perf_counter() - t0
+        t_sn, it_s, ok_s = 0.0, 0, 0
+        for i, op in enumerate(ops):
+            ui = torch.from_numpy(us[i]).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = op.newton_solve(ui, rtol=1e-8, inner_precision=32, raise_on_error=False)
+            torch.cuda.synchronize()
+            t_sn += time.perf_counter() - t0
+            it_s += r["cg_iters"]
+            ok_s += r["status"] == "FE_OK"
+        out["newton"] = {"batched_s": round(t_bn, 4), "batched_status": tot["status"],
+                         "batched_converged": sum(r["status"] == "FE_OK" for r in reps),
+                         "batched_max_newton_steps": tot["newton_iters"], "batched_cg_iters": tot["cg_iters"],
+                         "batched_max_rel_residual": max(r["rel"] for r in reps),
+                         "batched_launches": tot["launches"],
+                         "sequential_s": round(t_sn, 4), "sequential_converged": ok_s, "sequential_cg_iters": it_s,
+                         "batching_speedup_newton": round(t_sn / t_bn, 3)}
+    for op in ops:
+        op.close()
+    B.close()
+    return out
+
+
 # ------------------------------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline / reference arm)
 # ------------------------------------------------------------------------------------------------
@@ -550,15 +635,16 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-newton", type=int, default=50)
-    ap.add_argument("--suite", choices=["headline", "sweep", "design"], default="headline",
-                    help="headline (the benchmark line), sweep (orders 1-6) or design (adjoint case)")
+    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched"], default="headline",
+                    help="headline (the benchmark line), sweep (orders 1-6), design (adjoint case) or "
+                         "batched (64 instances in one persistent launch)")
     ap.add_argument("--orders", default="1,2,3,4,5,6")
     ap.add_argument("--fd-dirs", type=int, default=20)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.suite != "headline" and args.impl == "gpu":
-        out = run_sweep(args) if args.suite == "sweep" else run_design(args)
+        out = {"sweep": run_sweep, "design": run_design, "batched": run_batched}[args.suite](args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:

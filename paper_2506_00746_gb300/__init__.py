@@ -14,7 +14,7 @@ import numpy as np
 from . import abi, inputs
 from .abi import FeodError
 
-__all__ = ["Operator", "ComplianceFn", "FeodError", "abi", "inputs", "build_library"]
+__all__ = ["Operator", "Batch", "ComplianceFn", "FeodError", "abi", "inputs", "build_library"]
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
@@ -171,6 +171,118 @@ class Operator:
         if getattr(self, "ctx", None):
             abi.fe_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent 3D instances of order 1..4 in one persistent launch (a ``fe_batch``).
+
+    ``instances``: list of dicts with keys ``vertices`` (host [(n+1)^3, 3]), ``n``, ``order`` and
+    optionally ``p`` (3.0), ``eps`` (0.0), ``f_kind`` (0), ``f_const`` (1.0).  Batch vectors are
+    the instances' vectors concatenated at ``offsets`` (see ``split``/``concat``).  ``tune``:
+    autotune tile edges and launch shape (cached in ``tune_cache``); ``tiles``: per order 1..4 a
+    fixed tile edge (0 = tuned).
+    """
+
+    def __init__(self, instances, tune: bool = True, tune_cache: str | None = None, retune: bool = False,
+                 policy: int = -1, tiles=None):
+        import ctypes
+
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Batch needs a CUDA device: the library has no CPU path")
+        self.count = len(instances)
+        self._keep = []
+        items = (abi.fe_batch_item * self.count)()
+        for i, d in enumerate(instances):
+            vert = np.ascontiguousarray(d["vertices"], dtype=np.float64)
+            mesh = abi.fe_mesh(3, int(d["n"]), vert.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+            prob = abi.fe_problem(float(d.get("p", 3.0)), float(d.get("eps", 0.0)), int(d.get("f_kind", 0)),
+                                  float(d.get("f_const", 1.0)), None, 1e-3, 3.0)
+            self._keep += [vert, mesh, prob]
+            items[i].mesh = ctypes.pointer(mesh)
+            items[i].order = int(d["order"])
+            items[i].prob = ctypes.pointer(prob)
+        opts = abi.fe_batch_opts()
+        self._cache = tune_cache.encode() if tune_cache else None
+        opts.tune_cache = self._cache
+        opts.tune, opts.retune, opts.policy = int(bool(tune)), int(bool(retune)), int(policy)
+        for k in range(4):
+            opts.tile[k] = int(tiles[k]) if tiles else 0
+        self.batch = abi.fe_batch_create(items, self.count, opts)
+        info = [abi.fe_batch_info(self.batch, i) for i in range(self.count)]
+        self.offsets = [o for o, _, _ in info]
+        self.n_dofs = [n for _, n, _ in info]
+        self.tiles = [t for _, _, t in info]
+        self.orders = [int(d["order"]) for d in instances]
+        self.total = abi.fe_batch_shape(self.batch)["total"]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def shape(self) -> dict:
+        return abi.fe_batch_shape(self.batch)
+
+    def vector(self, dtype=None):
+        import torch
+        return torch.zeros(self.total, dtype=dtype or torch.float64, device=self.device)
+
+    def split(self, vec) -> list:
+        return [vec[o:o + n] for o, n in zip(self.offsets, self.n_dofs)]
+
+    def concat(self, parts, dtype=None):
+        import torch
+        v = self.vector(dtype)
+        for o, n, x in zip(self.offsets, self.n_dofs, parts):
+            v[o:o + n] = torch.as_tensor(x, dtype=v.dtype).to(self.device)
+        return v
+
+    def _chk(self, t, dtype, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+                and t.numel() == self.total):
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} batch vector of {self.total} entries")
+        return t
+
+    def linearize(self, u, stream=None):
+        import torch
+        abi.fe_batch_linearize(self.batch, self._chk(u, torch.float64, "u"), stream)
+
+    def jacobian_action(self, v, out=None, stream=None):
+        import torch
+        y = out if out is not None else self.vector(torch.float32)
+        abi.fe_batch_jacobian_action(self.batch, self._chk(v, torch.float32, "v"), self._chk(y, torch.float32, "y"),
+                                     stream)
+        return y
+
+    def newton_solve(self, u, rtol: float = 1e-8, cg_rtol: float = 1e-4, max_newton: int = 50,
+                     max_cg: int = 20000, cg_batch: int = 16, use_graph: bool = True, line_search: bool = True,
+                     raise_on_error: bool = True, stream=None):
+        """Newton on every instance in lock step (FP32 CG, FP64 outer); returns (reports, total)."""
+        import torch
+        self._chk(u, torch.float64, "u")
+        o = abi.fe_newton_default_opts()
+        o.rtol, o.cg_rtol, o.max_newton, o.max_cg = rtol, cg_rtol, max_newton, max_cg
+        o.cg_batch, o.use_graph, o.line_search, o.inner_precision = cg_batch, int(use_graph), int(line_search), 32
+        reps, tot, err = abi.fe_batch_newton_solve(self.batch, u, self.count, o, stream)
+        conv = lambda r: {"status": abi.STATUS_NAMES.get(r.status, r.status), "newton_iters": r.newton_iters,
+                          "cg_iters": r.cg_iters_total, "r0": r.r0, "r_final": r.r_final,
+                          "rel": r.r_final / r.r0 if r.r0 > 0 else 0.0, "halvings": r.line_search_halvings}
+        total = conv(tot)
+        total.update({"time_ms": tot.t_total_ms, "cg_ms": tot.t_cg_ms, "launches": tot.kernel_launches})
+        if tot.status != abi.FE_OK:
+            total["error"] = err
+            if raise_on_error:
+                raise FeodError(tot.status, "fe_batch_newton_solve", err)
+        return [conv(r) for r in reps], total
+
+    def close(self):
+        if getattr(self, "batch", None):
+            abi.fe_batch_destroy(self.batch)
+            self.batch = None
 
     def __del__(self):
         try:

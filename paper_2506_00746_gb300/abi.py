@@ -58,7 +58,17 @@ class fe_newton_report(ctypes.Structure):
                 ("r_hist", c_double * FE_NEWTON_HIST), ("cg_hist", c_int * FE_NEWTON_HIST)]
 
 
+class fe_batch_item(ctypes.Structure):
+    _fields_ = [("mesh", POINTER(fe_mesh)), ("order", c_int), ("prob", POINTER(fe_problem))]
+
+
+class fe_batch_opts(ctypes.Structure):
+    _fields_ = [("tune_cache", c_char_p), ("tune", c_int), ("retune", c_int), ("policy", c_int),
+                ("tile", c_int * 4)]
+
+
 _CTX = c_void_p
+_BATCH = c_void_p
 _SIGS = {
     "fe_setup": (c_int, [POINTER(fe_mesh), c_int, c_int, POINTER(fe_problem), POINTER(_CTX)]),
     "fe_setup_ex": (c_int, [POINTER(fe_mesh), c_int, c_int, POINTER(fe_problem), POINTER(fe_setup_opts),
@@ -87,6 +97,16 @@ _SIGS = {
     "fe_destroy": (None, [_CTX]),
     "fe_last_error": (c_char_p, [_CTX]),
     "fe_status_string": (c_char_p, [c_int]),
+    "fe_batch_create": (c_int, [POINTER(fe_batch_item), c_int, POINTER(fe_batch_opts), POINTER(_BATCH)]),
+    "fe_batch_info": (c_int, [_BATCH, c_int, POINTER(c_int64), POINTER(c_int64), POINTER(c_int)]),
+    "fe_batch_shape": (c_int, [_BATCH, POINTER(c_int64), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                               POINTER(c_int64)]),
+    "fe_batch_linearize": (c_int, [_BATCH, c_void_p, c_void_p]),
+    "fe_batch_jacobian_action": (c_int, [_BATCH, c_void_p, c_void_p, c_void_p]),
+    "fe_batch_newton_solve": (c_int, [_BATCH, c_void_p, POINTER(fe_newton_opts), POINTER(fe_newton_report),
+                                      POINTER(fe_newton_report), c_void_p]),
+    "fe_batch_destroy": (None, [_BATCH]),
+    "fe_batch_last_error": (c_char_p, [_BATCH]),
 }
 
 _LIB = None
@@ -264,4 +284,62 @@ def fe_destroy(ctx):
 
 def fe_last_error(ctx=None) -> str:
     m = library().fe_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# ---- batched instances ---------------------------------------------------------------------
+
+def _bcheck(status: int, where: str, batch=None) -> None:
+    if status != FE_OK:
+        msg = library().fe_batch_last_error(batch)
+        raise FeodError(status, where, msg.decode() if msg else "")
+
+
+def fe_batch_create(items, count: int, opts: fe_batch_opts | None = None):
+    b = _BATCH()
+    _bcheck(library().fe_batch_create(items, count, byref(opts) if opts is not None else None, byref(b)),
+            "fe_batch_create")
+    return b
+
+
+def fe_batch_info(batch, i: int) -> tuple[int, int, int]:
+    off, n, tile = c_int64(), c_int64(), c_int()
+    _bcheck(library().fe_batch_info(batch, i, byref(off), byref(n), byref(tile)), "fe_batch_info", batch)
+    return off.value, n.value, tile.value
+
+
+def fe_batch_shape(batch) -> dict:
+    tot, grid, thr, pol, ln = c_int64(), c_int(), c_int(), c_int(), c_int64()
+    _bcheck(library().fe_batch_shape(batch, byref(tot), byref(grid), byref(thr), byref(pol), byref(ln)),
+            "fe_batch_shape", batch)
+    return {"total": tot.value, "grid": grid.value, "threads": thr.value, "policy": pol.value,
+            "launches": ln.value}
+
+
+def fe_batch_linearize(batch, u, stream=None):
+    _bcheck(library().fe_batch_linearize(batch, ptr(u), stream_handle(stream)), "fe_batch_linearize", batch)
+
+
+def fe_batch_jacobian_action(batch, v, y, stream=None):
+    _bcheck(library().fe_batch_jacobian_action(batch, ptr(v), ptr(y), stream_handle(stream)),
+            "fe_batch_jacobian_action", batch)
+
+
+def fe_batch_newton_solve(batch, u, count: int, opts: fe_newton_opts | None = None, stream=None):
+    reps = (fe_newton_report * count)()
+    tot = fe_newton_report()
+    st = library().fe_batch_newton_solve(batch, ptr(u), byref(opts) if opts is not None else None, reps,
+                                         byref(tot), stream_handle(stream))
+    tot.status = st
+    err = library().fe_batch_last_error(batch).decode() if st != FE_OK else ""
+    return list(reps), tot, err
+
+
+def fe_batch_destroy(batch):
+    if batch:
+        library().fe_batch_destroy(batch)
+
+
+def fe_batch_last_error(batch=None) -> str:
+    m = library().fe_batch_last_error(batch)
     return m.decode() if m else ""

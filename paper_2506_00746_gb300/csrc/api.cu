@@ -302,6 +302,30 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
 
 }  // namespace
 
+namespace feod {
+fe_status residual_tangent32(fe_ctx *c, const double *u, double *r, cudaStream_t st)
+{
+    fe_status s = ensure_tangent(c, false, true);
+    if (s != FE_OK) return s;
+    c->ops->residual(c, u, r, nullptr, c->d_T32, st);
+    CKLAUNCH();
+    c->lin32 = true;
+    return FE_OK;
+}
+
+fe_status jacobi_diag32(fe_ctx *c, double *d, cudaStream_t st)
+{
+    if (!c->lin32) return fail(c, FE_ERR_STATE, "no FP32 linearisation");
+    c->ops->diag_32(c, d, st);
+    CKLAUNCH();
+    return FE_OK;
+}
+
+fe_status set_error(fe_ctx *c, fe_status s, const char *msg) { return fail(c, s, "%s", msg); }
+
+fe_status alloc_tangent32(fe_ctx *c) { return ensure_tangent(c, false, true); }
+}  // namespace feod
+
 // ------------------------------------------------------------------------------------------------
 // setup
 // ------------------------------------------------------------------------------------------------

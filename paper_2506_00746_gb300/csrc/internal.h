@@ -210,6 +210,15 @@ struct fe_ctx {
 
 namespace feod {
 
+// Library-internal calls on one context (implemented in api.cu), used by the batch runtime.
+// residual_tangent32: R(u) into r (nullptr: none) and the FP32 quadrature-point tangent at u,
+// fused; jacobi_diag32: diag(J) from the stored FP32 tangent.  Both stream-ordered on st.
+fe_status residual_tangent32(fe_ctx *c, const double *u, double *r, cudaStream_t st);
+fe_status jacobi_diag32(fe_ctx *c, double *d, cudaStream_t st);
+fe_status set_error(fe_ctx *c, fe_status s, const char *msg);
+// alloc_tangent32: the (zero-filled) FP32 tangent storage, without computing it
+fe_status alloc_tangent32(fe_ctx *c);
+
 // Profiling bracket around one kernel launch.
 int prof_name_id(fe_ctx *c, const char *name);
 void prof_begin(fe_ctx *c, int name_id, cudaStream_t st, cudaEvent_t *a);

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     using TS = TileShape<D1, TT>;
     constexpr int NS3 = TS::NS3, NA = TS::NA, NC = TS::NC, NSX = TS::NSX, NSY = TS::NSY, NTH = TS::THREADS;
     if (P.skip && *P.skip) return;
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int64_t t = blockIdx.x;
     const int tid = threadIdx.x;
     const int64_t tqs = tq_stride<TC>(P);
@@ -385,25 +385,45 @@ __host__ __device__ inline size_t tile2_smem_bytes(int64_t tqs)
            pad16((size_t)TS::NSZ * 4);
 }
 
+// Barrier policies of the packed tile code: the whole CTA, or one named barrier over a group of
+// threads (a CTA that runs several tiles at once, each on its own thread group).
+struct CtaBar {
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+};
+struct GroupBar {
+    int id, count;      // barrier 1..15 (0 is __syncthreads'), threads (a multiple of 32)
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory"); }
+    __device__ __forceinline__ bool any(bool p) const
+    {
+        int r;
+        asm volatile("{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, %2, %3, pi;\n\t"
+                     "selp.u32 %0, 1, 0, po;\n\t}"
+                     : "=r"(r) : "r"((int)p), "r"(id), "r"(count) : "memory");
+        return r != 0;
+    }
+};
+
 // store_hd() runs after the z stage: it stores the halo positions that the prologue loaded into
 // registers (their latency overlaps the z stage; they are read only by the writes).
 // tangent_ready() runs in every thread before the x stage (the first reader of Tb) and returns
 // false, uniformly, to abandon the tile.
-template <int D1, int TT, typename TIO, typename StoreHd, typename Ready>
+template <int D1, int TT, typename TIO, typename Bar, typename StoreHd, typename Ready>
 __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *Tb, const TIO *Vs,
                                              const uint32_t *codes, const uint32_t *hd, float2 *A2, float *C1,
                                              float2 *C2, float *SX1, float2 *SX2, float2 *SY2, float *SZ1,
                                              const TIO *__restrict__ v, TIO *__restrict__ y,
-                                             float *__restrict__ halo, int tid, StoreHd store_hd,
-                                             Ready tangent_ready)
+                                             float *__restrict__ halo, int tid, const Bar &bar,
+                                             StoreHd store_hd, Ready tangent_ready)
 {
     using TS = TileShape2<D1, TT>;
     constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT;
     constexpr int SA2 = TS::SA2, NLP = TS::NLP;
     const int L = tid % NLP, h = tid / NLP;
+    const bool live = h < TT;      // threads past the variant's count only take part in barriers
 
     // z: segment h of line (sx, sy): (B v, G v) at Q1 points
-    if (L < SE * SE) {
+    if (live && L < SE * SE) {
         const int sx = L % SE, sy = L / SE;
         float in[D1];
 #pragma unroll
@@ -417,9 +437,9 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
         }
     }
     store_hd();
-    __syncthreads();
+    bar.sync();
     // y: segment h of line (sx, qz)
-    if (L < SE * QT) {
+    if (live && L < SE * QT) {
         const int sx = L % SE, qz = L / SE;
         float2 a2[D1];
 #pragma unroll
@@ -438,12 +458,12 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
             C2[o] = cp;
         }
     }
-    __syncthreads();
+    bar.sync();
     // x: segment h of line (qy, qz): gradient, D, x transpose
     if (!tangent_ready()) return false;
     float d00[D1];
     float2 dp[D1];
-    const bool actx = L < QT * QT;
+    const bool actx = live && L < QT * QT;
     const int xqz = L % QT, xqy = L / QT;
     const int xo = SE * xqz + SE * QT * xqy + K * h;
     if (actx) {
@@ -482,7 +502,7 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
             }
         }
     }
-    __syncthreads();       // every segment has read its c values before any is overwritten
+    bar.sync();       // every segment has read its c values before any is overwritten
     if (actx) {
 #pragma unroll
         for (int a = 0; a < K; ++a) { C1[xo + a] = d00[a]; C2[xo + a] = dp[a]; }
@@ -493,9 +513,9 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
             SX1[so] = d00[K]; SX2[so] = dp[K];
         }
     }
-    __syncthreads();
+    bar.sync();
     // y transpose: segment h of line (sx, qz)
-    if (L < SE * QT) {
+    if (live && L < SE * QT) {
         const int sx = L % SE, qz = L / SE;
         const bool xseam = (sx % K == 0) && sx > 0 && sx < SE - 1;
         float e00[Q1];
@@ -526,10 +546,10 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
         if (h == TT - 1) A2[sx + SE * qz + SA2 * (SE - 1)] = E[K];
         else SY2[h * QT * SE + L] = E[K];
     }
-    __syncthreads();
+    bar.sync();
     // z transpose: segment h of line (sx, sy); P^T and the writes
     float out[D1];
-    const bool actz = L < SE * SE;
+    const bool actz = live && L < SE * SE;
     const int zx = L % SE, zy = L / SE;
     auto write_slot = [&](int sz, float val) {
         const int s = (sz * SE + zy) * SE + zx;
@@ -568,29 +588,29 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
         if (h == TT - 1) write_slot(SE - 1, out[K]);
         else SZ1[h * SE * SE + L] = out[K];
     }
-    __syncthreads();
+    bar.sync();
     if (actz && h > 0) write_slot(K * h, SZ1[(h - 1) * SE * SE + L] + out[0]);
     return true;
 }
 
-// One CTA per tile (FP32 compute; TIO float or double), as k_jv_tile.
-template <int D1, int TT, typename TIO>
-__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
-    k_jv_tile2(const __grid_constant__ OpParams P, const __grid_constant__ BasisPairs Pr,
-               const float *__restrict__ Tq, const TIO *__restrict__ v, TIO *__restrict__ y,
-               float *__restrict__ halo)
+// One tile of the FP32 packed variant on a group of threads (tid: the thread's index in the group,
+// bar: the group's barrier) of at least TileShape<D1, TT>::THREADS threads (the extra threads
+// take part only in barriers).  smem: the tile's shared region (after the
+// mbarrier); mbar: an initialised mbarrier whose phase `parity` this tile's tangent copy
+// completes.  Returns false (uniformly) when the tangent copy did not land within the bound;
+// the caller then reports and waits for it again.
+template <int D1, int TT, typename TIO, typename Bar>
+__device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &Pr, const float *__restrict__ Tq,
+                                           const TIO *__restrict__ v, TIO *__restrict__ y,
+                                           float *__restrict__ halo, int64_t t, unsigned char *smem,
+                                           uint64_t *mbar, uint32_t parity, int tid, const Bar &bar)
 {
     using TS = TileShape2<D1, TT>;
     constexpr int NS3 = TS::NS3, NTH = TS::THREADS;
-    if (P.skip && *P.skip) return;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int64_t t = blockIdx.x;
-    const int tid = threadIdx.x;
     const int64_t tqs = tq_stride<float>(P);
     const uint32_t tq_bytes = (uint32_t)(tqs * sizeof(float));
 
     unsigned char *p = smem;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(p);    p += 64;
     float *Tb = reinterpret_cast<float *>(p);           p += pad16(tq_bytes);
     uint32_t *codes = reinterpret_cast<uint32_t *>(p);  p += pad16(NS3 * 4);
     uint32_t *hd = reinterpret_cast<uint32_t *>(p);     p += pad16(NS3 * 4);
@@ -604,8 +624,6 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     float *SZ1 = reinterpret_cast<float *>(p);
 
     if (tid == 0) {
-        mbar_init(mbar, 1);
-        fence_mbar_init();
         mbar_arrive_expect_tx(mbar, tq_bytes);
         tma_load_1d(Tb, Tq + t * tqs, tq_bytes, mbar);
     }
@@ -613,6 +631,7 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     // halo-array positions, which reach shared memory after the z stage
     constexpr int NPER = (NS3 + NTH - 1) / NTH;
     uint32_t hr[NPER];
+    const bool gth = tid < NTH;
     {
         const uint32_t *sl = P.slot + t * P.Spad;
         const uint32_t *hs = P.hdst + t * P.Spad;
@@ -620,7 +639,7 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
 #pragma unroll
         for (int i = 0; i < NPER; ++i) {
             const int s = tid + i * NTH;
-            cr[i] = s < NS3 ? sl[s] : SLOT_INVALID;
+            cr[i] = gth && s < NS3 ? sl[s] : SLOT_INVALID;
         }
         TIO vr[NPER];
 #pragma unroll
@@ -631,23 +650,42 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
 #pragma unroll
         for (int i = 0; i < NPER; ++i) {
             const int s = tid + i * NTH;
-            if (s < NS3) { codes[s] = cr[i]; Vs[s] = vr[i]; }
+            if (gth && s < NS3) { codes[s] = cr[i]; Vs[s] = vr[i]; }
         }
     }
-    // makes thread 0's mbarrier initialisation and the gathered block visible to all threads;
-    // the tangent block is waited for (bounded) only before the x stage, its first reader
-    __syncthreads();
-    const bool ok = tile_stages2<D1, TT, TIO>(
-        Pr, Tb, Vs, codes, hd, A2, C1, C2, SX1, SX2, SY2, SZ1, v, y, halo, tid,
+    // makes the gathered block (and, in a new CTA, the mbarrier initialisation) visible to all
+    // threads; the tangent block is waited for (bounded) only before the x stage, its first reader
+    bar.sync();
+    return tile_stages2<D1, TT, TIO>(
+        Pr, Tb, Vs, codes, hd, A2, C1, C2, SX1, SX2, SY2, SZ1, v, y, halo, tid, bar,
         [&]() {
 #pragma unroll
             for (int i = 0; i < NPER; ++i) {
                 const int s = tid + i * NTH;
-                if (s < NS3) hd[s] = hr[i];
+                if (gth && s < NS3) hd[s] = hr[i];
             }
         },
-        [&]() { return !__syncthreads_or(!mbar_wait_bounded(mbar, 0)); });
-    if (!ok && tid == 0) {
+        [&]() { return !bar.any(!mbar_wait_bounded(mbar, parity)); });
+}
+
+// One CTA per tile (FP32 compute; TIO float or double), as k_jv_tile.
+template <int D1, int TT, typename TIO>
+__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
+    k_jv_tile2(const __grid_constant__ OpParams P, const __grid_constant__ BasisPairs Pr,
+               const float *__restrict__ Tq, const TIO *__restrict__ v, TIO *__restrict__ y,
+               float *__restrict__ halo)
+{
+    if (P.skip && *P.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+    // thread 0 initialises the barrier before it issues the copy; the other threads poll it only
+    // after the body's first __syncthreads
+    if (!tile2_body<D1, TT, TIO>(P, Pr, Tq, v, y, halo, blockIdx.x, smem + 64, mbar, 0u, tid, CtaBar{}) && tid == 0) {
         // the tangent block did not land within the bound: report, let the copy finish
         atomicExch(P.err, 3);
         mbar_wait_bounded(mbar, 0);
