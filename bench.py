@@ -278,7 +278,7 @@ def run_gpu(args) -> dict | None:
     peaks = measured_peaks()
     bytes_alg = jv_algorithmic_bytes(nl, ne, nq, nq, 4)
     achieved = bytes_alg / t_main / 1e9
-    kname = "k_jv_tile<4,2,float,float>"
+    kname = "k_jv_tile2<4,2,float>"
     traffic, traffic_src = profiled_traffic(kname)
     out = {
         "metric": METRIC,
@@ -554,6 +554,54 @@ def run_batched(args) -> dict:
     return out
 
 
+def run_jv_small(args) -> dict:
+    """A few Jacobian actions of one 3D p=3 instance (the small cases the ncu captures use): n
+    elements per direction, order, precision 64 / 32 / -32, `reps` actions after linearising at
+    the seeded smooth state."""
+    import torch
+
+    from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    V = I.lattice_vertices(3, args.n, seed=0)
+    op = Operator(3, args.n, args.order, V, p=3.0)
+    u = torch.from_numpy(I.smooth_field(3, args.n, args.order, seed=1)).cuda()
+    op.linearize(u)
+    v = torch.from_numpy(I.uniform_vector(op.n_dofs, seed=2)).cuda()
+    if args.precision == 32:
+        v = v.float()
+    for _ in range(args.reps):
+        y = op.jacobian_action(v, precision=args.precision)
+    torch.cuda.synchronize()
+    out = {"suite": "jv", "n": args.n, "order": args.order, "precision": args.precision, "reps": args.reps,
+           "n_dofs": op.n_dofs, "norm": float(y.double().norm())}
+    op.close()
+    return out
+
+
+def run_batch_subset(args) -> dict:
+    """A few batched Jacobian actions on the first `instances` of the 64-instance set (no tuning:
+    largest tile edges, largest instances first)."""
+    import torch
+
+    from paper_2506_00746_gb300 import Batch
+    from paper_2506_00746_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    ws = I.batched_instances(64, seed=5)[:args.instances]
+    inst = [{"vertices": I.lattice_vertices(3, w.n, seed=w.mesh_seed), "n": w.n, "order": w.order, "p": w.p}
+            for w in ws]
+    B = Batch(inst, tune=False, policy=2)
+    B.linearize(B.concat([I.smooth_field(3, w.n, w.order, seed=w.state_seed) for w in ws]))
+    v = B.concat([I.uniform_vector(n, seed=w.dir_seed) for n, w in zip(B.n_dofs, ws)], torch.float32)
+    for _ in range(args.reps):
+        y = B.jacobian_action(v)
+    torch.cuda.synchronize()
+    out = {"suite": "batch-subset", "instances": args.instances, "n_dofs": sum(B.n_dofs), "launch": B.shape(),
+           "norm": float(y.double().norm())}
+    B.close()
+    return out
+
+
 # ------------------------------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline / reference arm)
 # ------------------------------------------------------------------------------------------------
@@ -635,16 +683,24 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-newton", type=int, default=50)
-    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched"], default="headline",
-                    help="headline (the benchmark line), sweep (orders 1-6), design (adjoint case) or "
-                         "batched (64 instances in one persistent launch)")
+    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "jv", "batch-subset"],
+                    default="headline",
+                    help="headline (the benchmark line), sweep (orders 1-6), design (adjoint case), batched "
+                         "(64 instances in one persistent launch); jv and batch-subset run the small cases "
+                         "of the ncu captures")
+    ap.add_argument("--n", type=int, default=48)
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--precision", type=int, default=32)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--instances", type=int, default=24)
     ap.add_argument("--orders", default="1,2,3,4,5,6")
     ap.add_argument("--fd-dirs", type=int, default=20)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.suite != "headline" and args.impl == "gpu":
-        out = {"sweep": run_sweep, "design": run_design, "batched": run_batched}[args.suite](args)
+        out = {"sweep": run_sweep, "design": run_design, "batched": run_batched, "jv": run_jv_small,
+               "batch-subset": run_batch_subset}[args.suite](args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
