@@ -554,6 +554,38 @@ def run_batched(args) -> dict:
     return out
 
 
+def run_element_ad(args) -> dict:
+    """Element tangent matrices K_e (Eq. 3) on hexahedra of orders 1-3, formed by the hand-coded
+    tangent (HND), quadrature-point AD (RES) and element-level AD (ELM): time per element."""
+    import torch
+
+    from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    rows = []
+    for k, n in ((1, 48), (2, 32), (3, 24)):
+        V = I.lattice_vertices(3, n, seed=0)
+        op = Operator(3, n, k, V, p=3.0)
+        u = torch.from_numpy(I.smooth_field(3, n, k, seed=1)).cuda()
+        ne, nl = op.n_elements, (k + 1) ** 3
+        nc = 8
+        # flops of each implementation (multiply-add = 2): point gradients + tangent, then
+        # sum_q G^T (T G); ELM: ceil(nl / 8) passes of the dual B and B^T (9 components each)
+        f_res = nl * 6 * nl + nl * nl * (18 + 6 * nl)
+        f_elm = -(-nl // nc) * (2 * nl * nl * 3 * 2 * (nc + 1))
+        row = {"order": k, "n": n, "elements": ne, "nl": nl, "flop_res_per_elem": f_res,
+               "flop_elm_per_elem": f_elm}
+        for m in ("hnd", "res", "elm"):
+            t = _event_time(lambda: op.element_matrices(u, m), 3, 1)
+            row[f"{m}_us_per_elem"] = round(t / ne * 1e6, 5)
+        row["elm_over_res"] = round(row["elm_us_per_elem"] / row["res_us_per_elem"], 3)
+        row["res_over_hnd"] = round(row["res_us_per_elem"] / row["hnd_us_per_elem"], 3)
+        rows.append(row)
+        op.close()
+        torch.cuda.empty_cache()
+    return {"suite": "element-ad", "note": "dense element tangents; one CTA loops over elements", "orders": rows}
+
+
 def run_jv_small(args) -> dict:
     """A few Jacobian actions of one 3D p=3 instance (the small cases the ncu captures use): n
     elements per direction, order, precision 64 / 32 / -32, `reps` actions after linearising at
@@ -683,7 +715,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-newton", type=int, default=50)
-    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "jv", "batch-subset"],
+    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "element-ad", "jv", "batch-subset"],
                     default="headline",
                     help="headline (the benchmark line), sweep (orders 1-6), design (adjoint case), batched "
                          "(64 instances in one persistent launch); jv and batch-subset run the small cases "
@@ -699,7 +731,8 @@ def main(argv=None):
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.suite != "headline" and args.impl == "gpu":
-        out = {"sweep": run_sweep, "design": run_design, "batched": run_batched, "jv": run_jv_small,
+        out = {"sweep": run_sweep, "design": run_design, "batched": run_batched, "element-ad": run_element_ad,
+               "jv": run_jv_small,
                "batch-subset": run_batch_subset}[args.suite](args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -177,6 +177,19 @@ fe_status fe_set_design(fe_ctx *ctx, const double *rho, void *stream);
 fe_status fe_adjoint_vjp(fe_ctx *ctx, const double *u, const double *lambda, double *grad_rho,
                          void *stream);
 
+/* fe_element_matrices: dense element tangent matrices K_e = dr_e/du_e = B^T J_D(u_q) B (Eq. 3) of
+ * the elements [e0, e0 + count) (lexicographic element order, x fastest) at the state u, each
+ * [nl][nl] row-major in the local DOF order a + D1 (b + D1 c) (D1 = order + 1), no Dirichlet
+ * convention.  The comparison of where the AD sits (Table 1's columns), not a solver path:
+ *   method 0 (HND): the law's tangent written out by hand at each quadrature point;
+ *   method 1 (RES): forward AD at the quadrature point (the law on dim dual directions);
+ *   method 2 (ELM): forward AD at the element level (the element residual on dual numbers over
+ *                   the element DOFs, 8 directions per pass, B and B^T inside the AD).
+ * HND and RES form K_e = sum_q G_q^T T_q G_q with dense reference-gradient tables.  3D, order 1..3
+ * (FE_ERR_UNSUPPORTED otherwise).  u: device double[N_L]; K: device double[count * nl * nl]. */
+fe_status fe_element_matrices(fe_ctx *ctx, const double *u, int method, int64_t e0, int64_t count,
+                              double *K, void *stream);
+
 /* Newton-CG options.  Defaults (fe_newton_default_opts): rtol 1e-8, max_newton 50, max_cg 20000,
  * cg_rtol 1e-4, inner_precision 64, line_search 1, armijo 1e-4, max_halvings 20,
  * cg_batch 16, use_graph 1. */

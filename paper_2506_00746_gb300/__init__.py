@@ -121,6 +121,17 @@ class Operator:
                            self._chk(lam, torch.float64, name="lambda"), g, stream)
         return g
 
+    def element_matrices(self, u, method: str = "res", e0: int = 0, count: int | None = None, stream=None):
+        """Dense element tangents K_e (Eq. 3) of elements [e0, e0 + count): method "hnd" (hand-coded
+        tangent), "res" (AD at the quadrature point) or "elm" (AD at the element level)."""
+        import torch
+        count = self.n_elements - e0 if count is None else count
+        nl = (self.order + 1) ** self.dim
+        K = torch.empty((count, nl, nl), dtype=torch.float64, device=self.device)
+        abi.fe_element_matrices(self.ctx, self._chk(u, torch.float64, name="u"), {"hnd": 0, "res": 1, "elm": 2}[method],
+                                e0, count, K, stream)
+        return K
+
     # -- solvers ----------------------------------------------------------------------------
     def newton_solve(self, u, rtol: float = 1e-8, inner_precision: int = 64, cg_rtol: float = 1e-4,
                      max_newton: int = 50, max_cg: int = 20000, line_search: bool = True,

@@ -97,6 +97,7 @@ _SIGS = {
     "fe_destroy": (None, [_CTX]),
     "fe_last_error": (c_char_p, [_CTX]),
     "fe_status_string": (c_char_p, [c_int]),
+    "fe_element_matrices": (c_int, [_CTX, c_void_p, c_int, c_int64, c_int64, c_void_p, c_void_p]),
     "fe_batch_create": (c_int, [POINTER(fe_batch_item), c_int, POINTER(fe_batch_opts), POINTER(_BATCH)]),
     "fe_batch_info": (c_int, [_BATCH, c_int, POINTER(c_int64), POINTER(c_int64), POINTER(c_int)]),
     "fe_batch_shape": (c_int, [_BATCH, POINTER(c_int64), POINTER(c_int), POINTER(c_int), POINTER(c_int),
@@ -219,6 +220,11 @@ def fe_set_design(ctx, rho, stream=None):
 
 def fe_adjoint_vjp(ctx, u, lam, grad, stream=None):
     check(library().fe_adjoint_vjp(ctx, ptr(u), ptr(lam), ptr(grad), stream_handle(stream)), "fe_adjoint_vjp", ctx)
+
+
+def fe_element_matrices(ctx, u, method: int, e0: int, count: int, K, stream=None):
+    check(library().fe_element_matrices(ctx, ptr(u), method, e0, count, ptr(K), stream_handle(stream)),
+          "fe_element_matrices", ctx)
 
 
 def fe_newton_default_opts() -> fe_newton_opts:
