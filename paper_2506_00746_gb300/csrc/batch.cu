@@ -214,22 +214,49 @@ __global__ void k_fixup_batch(const BatchFix *__restrict__ bf, const int64_t *__
 {
     // the batched action before this kernel has taken all its packs: reset its counter
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= row0[count]) return;
-    int lo = 0, hi = count;          // row0[lo] <= r < row0[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) / 2;
-        if (row0[mid] <= r) lo = mid; else hi = mid;
+    const int64_t nrows = row0[count];
+    const int64_t rb = (int64_t)blockIdx.x * FIX_ROWS * blockDim.x + threadIdx.x;
+    // FIX_ROWS rows per thread, their loads issued before their use (as k_fixup)
+    float *yp[FIX_ROWS];
+    const float *hp[FIX_ROWS];
+    uint32_t g[FIX_ROWS], j0[FIX_ROWS], j1[FIX_ROWS];
+#pragma unroll
+    for (int i = 0; i < FIX_ROWS; ++i) {
+        const int64_t r = rb + (int64_t)i * blockDim.x;
+        j0[i] = j1[i] = 0u; g[i] = 0u; yp[i] = yb; hp[i] = nullptr;
+        if (r >= nrows) continue;
+        int lo = 0, hi = count;          // row0[lo] <= r < row0[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) / 2;
+            if (row0[mid] <= r) lo = mid; else hi = mid;
+        }
+        const BatchFix &B = bf[lo];
+        if (B.fix.skip && *B.fix.skip) continue;
+        const int64_t rr = r - row0[lo];
+        g[i] = B.fix.fix_g[rr];
+        j0[i] = B.fix.fix_off[rr];
+        j1[i] = B.fix.fix_off[rr + 1];
+        yp[i] = yb + B.off;
+        hp[i] = B.halo;
     }
-    const BatchFix &B = bf[lo];
-    if (B.fix.skip && *B.fix.skip) return;
-    const int64_t rr = r - row0[lo];
-    const uint32_t g = B.fix.fix_g[rr];
-    float *y = yb + B.off;
-    float acc = y[g];
-    const uint32_t j1 = B.fix.fix_off[rr + 1];
-    for (uint32_t j = B.fix.fix_off[rr]; j < j1; ++j) acc += B.halo[j];
-    y[g] = acc;
+    float acc[FIX_ROWS];
+    uint32_t kmax = 0;
+#pragma unroll
+    for (int i = 0; i < FIX_ROWS; ++i) {
+        acc[i] = j1[i] > j0[i] ? yp[i][g[i]] : 0.f;
+        kmax = max(kmax, j1[i] - j0[i]);
+    }
+    for (uint32_t k = 0; k < kmax; ++k) {
+        float h[FIX_ROWS];
+#pragma unroll
+        for (int i = 0; i < FIX_ROWS; ++i) h[i] = j0[i] + k < j1[i] ? hp[i][j0[i] + k] : 0.f;
+#pragma unroll
+        for (int i = 0; i < FIX_ROWS; ++i)
+            if (j0[i] + k < j1[i]) acc[i] += h[i];
+    }
+#pragma unroll
+    for (int i = 0; i < FIX_ROWS; ++i)
+        if (j1[i] > j0[i]) yp[i][g[i]] = acc[i];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -633,7 +660,7 @@ fe_status launch_jv(fe_batch *b, const float *vb, float *yb, bool with_skip, cud
     const BatchFix *fix = b->d_fix + (with_skip ? 0 : b->count);
     k_jv_batch<<<b->grid, BATCH_THREADS, b->smem, st>>>(inst, b->d_packs, b->npacks, vb, yb, b->d_err,
                                                          b->d_counter);
-    const unsigned fb = (unsigned)std::max<int64_t>(1, (b->nrows + 255) / 256);
+    const unsigned fb = (unsigned)std::max<int64_t>(1, (b->nrows + 256 * FIX_ROWS - 1) / (256 * FIX_ROWS));
     k_fixup_batch<<<fb, 256, 0, st>>>(fix, b->d_row0, b->count, yb, b->d_counter);
     b->launches += 2;
     BCK(cudaGetLastError());

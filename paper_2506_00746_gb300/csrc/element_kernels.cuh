@@ -321,18 +321,43 @@ __device__ __forceinline__ void scatter_tile(const OpParams &P, int64_t t, const
 }
 
 // Fix-up: y[g] = y[g] + sum of the halo partial sums of g, in ascending tile order, accumulated
-// in the compute type TC.
+// in the compute type TC.  Each thread takes FIX_ROWS rows (the rows of one load round are
+// consecutive across a warp) and issues the loads of all its rows before it uses them: the
+// kernel is bound by the latency of its dependent loads (row index -> value, halo entries).
+constexpr int FIX_ROWS = 4;
 template <typename TC, typename TIO>
 __global__ void k_fixup(const FixParams F, const TC *__restrict__ halo, TIO *__restrict__ y)
 {
     if (F.skip && *F.skip) return;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= F.nfix) return;
-    const uint32_t g = F.fix_g[r];
-    TC acc = (TC)y[g];
-    const uint32_t j1 = F.fix_off[r + 1];
-    for (uint32_t j = F.fix_off[r]; j < j1; ++j) acc += halo[j];
-    y[g] = (TIO)acc;
+    const int64_t r0 = (int64_t)blockIdx.x * FIX_ROWS * blockDim.x + threadIdx.x;
+    uint32_t g[FIX_ROWS], j0[FIX_ROWS], j1[FIX_ROWS];
+#pragma unroll
+    for (int i = 0; i < FIX_ROWS; ++i) {
+        const int64_t r = r0 + (int64_t)i * blockDim.x;
+        const bool ok = r < F.nfix;
+        g[i] = ok ? F.fix_g[r] : 0u;
+        j0[i] = ok ? F.fix_off[r] : 0u;
+        j1[i] = ok ? F.fix_off[r + 1] : 0u;
+    }
+    TC acc[FIX_ROWS];
+    uint32_t kmax = 0;
+#pragma unroll
+    for (int i = 0; i < FIX_ROWS; ++i) {
+        acc[i] = j1[i] > j0[i] ? (TC)y[g[i]] : TC(0);
+        kmax = max(kmax, j1[i] - j0[i]);
+    }
+    // halo entries in rounds: entry k of every row, in ascending order per row
+    for (uint32_t k = 0; k < kmax; ++k) {
+        TC h[FIX_ROWS];
+#pragma unroll
+        for (int i = 0; i < FIX_ROWS; ++i) h[i] = j0[i] + k < j1[i] ? halo[j0[i] + k] : TC(0);
+#pragma unroll
+        for (int i = 0; i < FIX_ROWS; ++i)
+            if (j0[i] + k < j1[i]) acc[i] += h[i];
+    }
+#pragma unroll
+    for (int i = 0; i < FIX_ROWS; ++i)
+        if (j1[i] > j0[i]) y[g[i]] = (TIO)acc[i];
 }
 
 // --------------------------------------------------------------------------------------------
@@ -967,7 +992,7 @@ struct Ops {
         if (c->nfix == 0) return;
         LaunchScope ls(c, "fixup", st);
         const int bs = 256;
-        const int64_t nb = (c->nfix + bs - 1) / bs;
+        const int64_t nb = (c->nfix + (int64_t)bs * FIX_ROWS - 1) / ((int64_t)bs * FIX_ROWS);
         k_fixup<TC, TIO><<<(unsigned)nb, bs, 0, st>>>(c->fix, reinterpret_cast<TC *>(c->d_halo), y);
     }
 
