@@ -23,7 +23,7 @@
 
 namespace feod {
 
-__host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ constexpr inline size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // pad of the y-slot stride of the z/y-stage arrays that makes all their accesses bank-conflict
 // free (found by exhaustive search over the access patterns of this kernel)
@@ -368,21 +368,28 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
 // Pair arrays use a y-slot stride congruent to SE mod 16, so that every half-warp's 64-bit access
 // touches 16 distinct bank pairs; the x stage's accesses have lane stride SE (odd) and are
 // conflict-free in both widths.
+// Shared-memory lifetimes let two regions double up: the gathered input block (read only by the
+// z stage) lives inside the x-stage pair array C2 (first written by the y stage), and the seam
+// planes (written from the x stage's end on) live inside the tangent buffer, which the x stage
+// has finished reading by then.
 template <int D1, int TT>
 struct TileShape2 : TileShape<D1, TT> {
     using B = TileShape<D1, TT>;
     static constexpr int SA2 = B::SE * B::QT + (((B::SE - B::SE * B::QT) % 16) + 16) % 16;
     static constexpr int NA2 = SA2 * B::SE;
+    static constexpr size_t SEAM_BYTES = pad16((size_t)B::NSX * 4) + pad16((size_t)B::NSX * 8) +
+                                         pad16((size_t)B::NSY * 8) + pad16((size_t)B::NSZ * 4);
+    static constexpr size_t TANGENT_MIN_BYTES = (size_t)6 * TT * TT * TT * D1 * D1 * D1 * 4;
 };
 
 template <int D1, int TT, typename TIO>
 __host__ __device__ inline size_t tile2_smem_bytes(int64_t tqs)
 {
     using TS = TileShape2<D1, TT>;
-    return 64 + pad16((size_t)tqs * 4) + 2 * pad16(TS::NS3 * 4) + pad16(TS::NS3 * sizeof(TIO)) +
-           pad16((size_t)TS::NA2 * 8) + pad16((size_t)TS::NC * 4) + pad16((size_t)TS::NC * 8) +
-           pad16((size_t)TS::NSX * 4) + pad16((size_t)TS::NSX * 8) + pad16((size_t)TS::NSY * 8) +
-           pad16((size_t)TS::NSZ * 4);
+    static_assert(TS::SEAM_BYTES <= TS::TANGENT_MIN_BYTES, "seam planes must fit in the tangent buffer");
+    static_assert((size_t)TS::NS3 * 8 <= (size_t)TS::NC * 8, "the input block must fit in C2");
+    return 64 + pad16((size_t)tqs * 4) + 2 * pad16(TS::NS3 * 4) + pad16((size_t)TS::NA2 * 8) +
+           pad16((size_t)TS::NC * 4) + pad16((size_t)TS::NC * 8);
 }
 
 // Barrier policies of the packed tile code: the whole CTA, or one named barrier over a group of
@@ -614,14 +621,15 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
     float *Tb = reinterpret_cast<float *>(p);           p += pad16(tq_bytes);
     uint32_t *codes = reinterpret_cast<uint32_t *>(p);  p += pad16(NS3 * 4);
     uint32_t *hd = reinterpret_cast<uint32_t *>(p);     p += pad16(NS3 * 4);
-    TIO *Vs = reinterpret_cast<TIO *>(p);               p += pad16(NS3 * sizeof(TIO));
     float2 *A2 = reinterpret_cast<float2 *>(p);         p += pad16((size_t)TS::NA2 * 8);
     float *C1 = reinterpret_cast<float *>(p);           p += pad16((size_t)TS::NC * 4);
-    float2 *C2 = reinterpret_cast<float2 *>(p);         p += pad16((size_t)TS::NC * 8);
-    float *SX1 = reinterpret_cast<float *>(p);          p += pad16((size_t)TS::NSX * 4);
-    float2 *SX2 = reinterpret_cast<float2 *>(p);        p += pad16((size_t)TS::NSX * 8);
-    float2 *SY2 = reinterpret_cast<float2 *>(p);        p += pad16((size_t)TS::NSY * 8);
-    float *SZ1 = reinterpret_cast<float *>(p);
+    float2 *C2 = reinterpret_cast<float2 *>(p);
+    TIO *Vs = reinterpret_cast<TIO *>(C2);              // z stage only; C2 is first written by y
+    unsigned char *q = reinterpret_cast<unsigned char *>(Tb);   // seams: after the x stage's reads
+    float *SX1 = reinterpret_cast<float *>(q);          q += pad16((size_t)TS::NSX * 4);
+    float2 *SX2 = reinterpret_cast<float2 *>(q);        q += pad16((size_t)TS::NSX * 8);
+    float2 *SY2 = reinterpret_cast<float2 *>(q);        q += pad16((size_t)TS::NSY * 8);
+    float *SZ1 = reinterpret_cast<float *>(q);
 
     if (tid == 0) {
         mbar_arrive_expect_tx(mbar, tq_bytes);
