@@ -17,10 +17,12 @@ constexpr int MAX_ORDER = 6;
 
 // Largest tile edge (elements per CTA = tile^dim) per (dim, order); also the default.  The
 // element kernels are compiled with launch bounds for this many elements per CTA, so a context
-// may use this tile or a smaller one.
+// may use this tile or a smaller one.  3D order 6 takes one-element tiles: a 2x2x2 tile of order 6
+// needs about 134 KB of shared memory in the FP32 tile kernel (one CTA per SM), a one-element tile
+// about 18 KB.
 constexpr int max_tile(int dim, int order)
 {
-    return dim == 3 ? (order == 1 ? 4 : order == 2 ? 3 : 2) : (order <= 3 ? 8 : 6);
+    return dim == 3 ? (order == 1 ? 4 : order == 2 ? 3 : order <= 5 ? 2 : 1) : (order <= 3 ? 8 : 6);
 }
 constexpr int max_threads(int dim, int order)
 {

@@ -287,8 +287,13 @@ __device__ __forceinline__ void tile_stages(const OpParams &P, const BasisT<TC> 
 // One CTA per tile.  Thread 0 starts the bulk copy of the tile's tangent block; meanwhile all
 // threads load the slot codes, then (in one batch) the input values and, for halo slots, their
 // halo-array positions.
+// small CTAs (one-element tiles of high order) get a register budget that leaves room for
+// several CTAs per SM: at most 128 registers per thread
+template <int THREADS>
+constexpr int tile_min_blocks() { return THREADS <= 128 ? 512 / THREADS : 1; }
+
 template <int D1, int TT, typename TC, typename TIO>
-__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
+__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<TileShape<D1, TT>::THREADS>())
     k_jv_tile(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs, const TC *__restrict__ Tq,
               const TIO *__restrict__ v, TIO *__restrict__ y, TC *__restrict__ halo)
 {
