@@ -101,9 +101,13 @@ struct BatchInst {
     int order;
 };
 
-// A pack: `count` consecutive tiles of one instance, run at once by the CTA's thread groups.
-struct Pack {
-    int inst, tile0, count, variant;
+// The work list: every tile of every instance as an item (instance, tile), grouped by variant:
+// items of variant v at [vbeg[v], vbeg[v+1]).  CTA b starts with variant start[b] and then takes
+// the others in cyclic order.
+struct Work {
+    const int2 *items;
+    int vbeg[NBV + 1];
+    const unsigned char *start;
 };
 
 // FP32 basis pairs per order 1..4 (identical for every instance of an order, so one copy serves
@@ -121,83 +125,84 @@ __device__ __noinline__ bool batch_item(const OpParams &P, const float *T32, con
     return tile2_body<D1, TT, float>(P, c_bpairs[D1 - 2], T32, v, y, halo, t, sm, mbar, parity, tid, bar);
 }
 
-// The persistent batched Jacobian action y = J v (FP32).  Each CTA takes packs from a global
-// counter until the list is exhausted (the batched fix-up resets the counter for the next
-// launch); thread group g of a pack runs tile tile0 + g with its own shared region, named
-// barrier 1 + g and mbarrier g, whose phase bit is kept in shared memory.  Packs of instances
-// whose skip flag is set are passed over.
+// The persistent batched Jacobian action y = J v (FP32).  A CTA works on one variant at a time,
+// split into 256 / threads independent thread groups; every group takes its next tile from the
+// variant's counter (group leader's atomic, broadcast through shared memory under the group's
+// named barrier 1 + g) and runs it with its own shared region and mbarrier g, whose phase bit is
+// kept in shared memory.  Groups never wait for each other except when the CTA moves on to the
+// next variant with work.  The batched fix-up resets the counters for the next launch.  Items of
+// instances whose skip flag is set are passed over.
 __global__ void __launch_bounds__(BATCH_THREADS, 4)
-    k_jv_batch(const BatchInst *__restrict__ inst,
-               const Pack *__restrict__ packs, int npacks, const float *__restrict__ vb, float *__restrict__ yb,
-               int *err, unsigned *counter)
+    k_jv_batch(const BatchInst *__restrict__ inst, const __grid_constant__ Work W, const float *__restrict__ vb,
+               float *__restrict__ yb, int *err, unsigned *counters)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);       // MAX_SLOTS mbarriers in 64 bytes
     __shared__ uint32_t s_par[MAX_SLOTS];
-    __shared__ Pack s_pk;
+    __shared__ int s_item[MAX_SLOTS];
     __shared__ int s_abort;
     const int tid = threadIdx.x;
-    // thread 0 runs the pack pipeline: the current pack's record in shared memory, the next pack's
-    // index and record in registers, fetched while the current pack computes
-    unsigned nxt = 0u;
-    Pack pn{ 0, 0, 0, -1 };
     if (tid == 0) {
         for (int k = 0; k < MAX_SLOTS; ++k) mbar_init(&mbar[k], 1);
         fence_mbar_init();
         s_abort = 0;
-        const unsigned cur = atomicAdd(counter, 1u);
-        s_pk = cur < (unsigned)npacks ? packs[cur] : Pack{ 0, 0, 0, -1 };
-        nxt = atomicAdd(counter, 1u);
     }
     if (tid < MAX_SLOTS) s_par[tid] = 0u;
-    for (;;) {
-        __syncthreads();
-        const Pack pk = s_pk;
-        if (pk.variant < 0 || s_abort) break;
-        if (tid == 0) pn = nxt < (unsigned)npacks ? packs[nxt] : Pack{ 0, 0, 0, -1 };   // consumed at the end
-        const BatchInst &I = inst[pk.inst];
-        if (!(I.op.skip && *I.op.skip)) {        // uniform: one flag, constant during the launch
-            const int nthr = bv_threads(pk.variant);
-            const int g = tid / nthr, lt = tid - g * nthr;
-            if (g < pk.count) {
-                const GroupBar bar{ 1 + g, nthr };
-                unsigned char *sm = smem + 64 + (size_t)g * bv_tile_bytes(pk.variant, I.op.tqs32);
-                const float *v = vb + I.off;
-                float *y = yb + I.off;
-                const int64_t t = pk.tile0 + g;
-                const uint32_t par = s_par[g];
-                bool ok;
-                switch (pk.variant) {
-                case 0: ok = batch_item<2, 4>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                case 1: ok = batch_item<2, 2>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                case 2: ok = batch_item<3, 2>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                case 3: ok = batch_item<3, 1>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                case 4: ok = batch_item<4, 2>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                case 5: ok = batch_item<4, 1>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                case 6: ok = batch_item<5, 2>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                default: ok = batch_item<5, 1>(I.op, I.T32, v, y, I.halo, t, sm, &mbar[g], par, lt, bar); break;
-                }
-                if (lt == 0) {
-                    if (ok) {
-                        s_par[g] = par ^ 1u;        // this group's copy completed one phase
-                    } else {
-                        // the tangent block did not land within the bound: report, let the copy
-                        // finish, and end the launch after this pack
-                        atomicExch(err, 3);
-                        mbar_wait_bounded(&mbar[g], par);
-                        s_abort = 1;
-                    }
+    __syncthreads();
+    const int v0 = W.start[blockIdx.x];
+    for (int vi = 0; vi < NBV; ++vi) {
+        const int v = (v0 + vi) % NBV;
+        const int nv = W.vbeg[v + 1] - W.vbeg[v];
+        if (nv == 0) continue;
+        const int nthr = bv_threads(v);
+        const int g = tid / nthr, lt = tid - g * nthr;
+        const GroupBar bar{ 1 + g, nthr };
+        uint64_t *mb = &mbar[g];
+        for (;;) {
+            if (lt == 0) s_item[g] = s_abort ? nv : (int)atomicAdd(&counters[v], 1u);
+            bar.sync();
+            const int idx = s_item[g];
+            if (idx >= nv) break;
+            const int2 it = W.items[W.vbeg[v] + idx];
+            const BatchInst &I = inst[it.x];
+            if (I.op.skip && *I.op.skip) {               // uniform in the group
+                bar.sync();                              // all have read s_item[g] before the next write
+                continue;
+            }
+            unsigned char *sm = smem + 64 + (size_t)g * bv_tile_bytes(v, I.op.tqs32);
+            const float *vin = vb + I.off;
+            float *y = yb + I.off;
+            const uint32_t par = s_par[g];
+            bool ok;
+            switch (v) {
+            case 0: ok = batch_item<2, 4>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            case 1: ok = batch_item<2, 2>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            case 2: ok = batch_item<3, 2>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            case 3: ok = batch_item<3, 1>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            case 4: ok = batch_item<4, 2>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            case 5: ok = batch_item<4, 1>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            case 6: ok = batch_item<5, 2>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            default: ok = batch_item<5, 1>(I.op, I.T32, vin, y, I.halo, it.y, sm, mb, par, lt, bar); break;
+            }
+            if (lt == 0) {
+                if (ok) {
+                    s_par[g] = par ^ 1u;                // this group's copy completed one phase
+                } else {
+                    // the tangent block did not land within the bound: report, let the copy finish,
+                    // and stop taking items
+                    atomicExch(err, 3);
+                    mbar_wait_bounded(mb, par);
+                    s_abort = 1;
                 }
             }
+            // this thread's shared-memory accesses are ordered before the group's next bulk copy,
+            // which may land where this tile kept other arrays
+            fence_proxy_async();
         }
-        // this thread's shared-memory accesses are ordered before the next pack's bulk copies,
-        // which may land where this pack kept other arrays
+        // every group is done with this variant before the CTA is re-partitioned for the next
         fence_proxy_async();
-        __syncthreads();                         // every group is done with s_pk and its region
-        if (tid == 0) {
-            s_pk = pn;
-            nxt = atomicAdd(counter, 1u);
-        }
+        __syncthreads();
+        if (s_abort) break;
     }
 }
 
@@ -212,8 +217,8 @@ struct BatchFix {
 __global__ void k_fixup_batch(const BatchFix *__restrict__ bf, const int64_t *__restrict__ row0, int count,
                               float *__restrict__ yb, unsigned *counter)
 {
-    // the batched action before this kernel has taken all its packs: reset its counter
-    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;
+    // the batched action before this kernel has taken all its items: reset its counters
+    if (blockIdx.x == 0 && threadIdx.x < NBV) counter[threadIdx.x] = 0u;
     const int64_t nrows = row0[count];
     const int64_t rb = (int64_t)blockIdx.x * FIX_ROWS * blockDim.x + threadIdx.x;
     // FIX_ROWS rows per thread, their loads issued before their use (as k_fixup)
@@ -473,11 +478,13 @@ struct fe_batch {
     // launch shape (autotuned)
     int grid = 0, threads = 0, policy = 0;
     size_t smem = 0;
-    int npacks = 0;
+    int ntotal_items = 0;
+    int vbeg[NBV + 1] = {};
     // device data
     BatchInst *d_inst = nullptr;          // two copies: [0, count) skip -> CG flags; [count, 2 count) none
-    Pack *d_packs = nullptr;
-    unsigned *d_counter = nullptr;        // pack counter of the batched action
+    int2 *d_items = nullptr;              // work items grouped by variant
+    unsigned char *d_start = nullptr;     // first variant of each CTA
+    unsigned *d_counter = nullptr;        // per-variant item counters of the batched action
     BatchFix *d_fix = nullptr;            // same two copies
     int64_t *d_row0 = nullptr;
     int64_t nrows = 0;
@@ -592,63 +599,86 @@ struct TuneCache {
 
 void free_batch_device(fe_batch *b)
 {
-    void *ptrs[] = { b->d_inst, b->d_packs, b->d_counter, b->d_fix, b->d_row0, b->d_seg_inst, b->d_blk0, b->d_seg_lo, b->d_seg_hi,
+    void *ptrs[] = { b->d_inst, b->d_items, b->d_start, b->d_counter, b->d_fix, b->d_row0, b->d_seg_inst, b->d_blk0, b->d_seg_lo, b->d_seg_hi,
                      b->d_len, b->d_active, b->d_err, b->d_state, b->d_partial, b->fx, b->fr, b->fp, b->fq, b->dinv,
                      b->R, b->Rt, b->B, b->D, b->diag };
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    b->d_inst = nullptr; b->d_packs = nullptr; b->d_counter = nullptr; b->d_fix = nullptr; b->d_row0 = nullptr; b->d_seg_inst = nullptr;
+    b->d_inst = nullptr; b->d_items = nullptr; b->d_start = nullptr; b->d_counter = nullptr; b->d_fix = nullptr; b->d_row0 = nullptr; b->d_seg_inst = nullptr;
     b->d_blk0 = nullptr; b->d_seg_lo = nullptr; b->d_seg_hi = nullptr; b->d_len = nullptr; b->d_active = nullptr;
     b->d_err = nullptr; b->d_state = nullptr; b->d_partial = nullptr; b->fx = b->fr = b->fp = b->fq = b->dinv = nullptr;
     b->R = b->Rt = b->B = b->D = b->diag = nullptr;
 }
 
-// the pack list: every tile of every instance in packs of up to bv_slots(variant) consecutive
-// tiles of one instance, in the order of `policy`
-//   0: instance by instance;  1: interleaved (each instance's packs spread evenly over the list);
+// the work list: every tile of every instance, grouped by variant; within a variant, by policy
+//   0: instance by instance;  1: interleaved (each instance's tiles spread evenly over the list);
 //   2: instances by decreasing DOF count (the largest first, the small ones fill the tail)
-std::vector<Pack> make_packs(const fe_batch *b, int policy)
+// and the first variant of every CTA, in proportion to the variants' estimated work
+fe_status upload_work(fe_batch *b, int policy)
 {
     const int n = b->count;
-    std::vector<std::vector<Pack>> per(n);
-    size_t tot = 0;
-    for (int i = 0; i < n; ++i) {
-        const int v = b->variant[i], P = bv_slots(v);
-        const int64_t nt = b->ctx[i]->ntiles;
-        for (int64_t t = 0; t < nt; t += P) per[i].push_back(Pack{ i, (int)t, (int)std::min<int64_t>(P, nt - t), v });
-        tot += per[i].size();
-    }
-    std::vector<Pack> w;
-    w.reserve(tot);
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     if (policy == 2)
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->len[x] > b->len[y]; });
-    if (policy != 1) {
-        for (int i : order) w.insert(w.end(), per[i].begin(), per[i].end());
-    } else {
-        std::vector<size_t> next(n, 0);
-        std::vector<double> pos(n);
-        for (int i = 0; i < n; ++i) pos[i] = per[i].empty() ? 2.0 : 0.5 / (double)per[i].size();
-        for (size_t k = 0; k < tot; ++k) {
-            int best = -1;
-            for (int i = 0; i < n; ++i)
-                if (next[i] < per[i].size() && (best < 0 || pos[i] < pos[best])) best = i;
-            w.push_back(per[best][next[best]]);
-            next[best]++;
-            pos[best] = next[best] < per[best].size() ? (next[best] + 0.5) / (double)per[best].size() : 2.0;
+    std::vector<std::vector<int2>> per(NBV);
+    for (int v = 0; v < NBV; ++v) {
+        std::vector<int> mine;
+        for (int i : order)
+            if (b->variant[i] == v) mine.push_back(i);
+        if (policy != 1) {
+            for (int i : mine)
+                for (int64_t t = 0; t < b->ctx[i]->ntiles; ++t) per[v].push_back(make_int2(i, (int)t));
+        } else {
+            std::vector<int64_t> next(mine.size(), 0);
+            std::vector<double> pos(mine.size());
+            int64_t tot = 0;
+            for (size_t j = 0; j < mine.size(); ++j) {
+                tot += b->ctx[mine[j]]->ntiles;
+                pos[j] = 0.5 / (double)b->ctx[mine[j]]->ntiles;
+            }
+            for (int64_t k = 0; k < tot; ++k) {
+                size_t best = 0;
+                for (size_t j = 1; j < mine.size(); ++j)
+                    if (pos[j] < pos[best]) best = j;
+                const int i = mine[best];
+                per[v].push_back(make_int2(i, (int)next[best]));
+                next[best]++;
+                pos[best] = next[best] < b->ctx[i]->ntiles ? (next[best] + 0.5) / (double)b->ctx[i]->ntiles : 2.0;
+            }
         }
     }
-    return w;
-}
-
-fe_status upload_work(fe_batch *b, int policy)
-{
-    const std::vector<Pack> w = make_packs(b, policy);
-    if (b->d_packs) { cudaFree(b->d_packs); b->d_packs = nullptr; }
-    BCK(balloc(&b->d_packs, w.size()));
-    BCK(cudaMemcpy(b->d_packs, w.data(), w.size() * sizeof(Pack), cudaMemcpyHostToDevice));
-    b->npacks = (int)w.size();
+    std::vector<int2> items;
+    double work[NBV];
+    for (int v = 0; v < NBV; ++v) {
+        b->vbeg[v] = (int)items.size();
+        items.insert(items.end(), per[v].begin(), per[v].end());
+        // a tile's cost grows with its elements and the contraction length: T^3 D1^4
+        work[v] = (double)per[v].size() * BV_TT[v] * BV_TT[v] * BV_TT[v] * std::pow((double)BV_D1[v], 4.0);
+    }
+    b->vbeg[NBV] = (int)items.size();
+    b->ntotal_items = (int)items.size();
+    if (b->d_items) { cudaFree(b->d_items); b->d_items = nullptr; }
+    BCK(balloc(&b->d_items, items.size()));
+    BCK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    // CTA b starts where the cumulative work share passes (b + 1/2) / grid
+    double wt = 0.0;
+    for (int v = 0; v < NBV; ++v) wt += work[v];
+    std::vector<unsigned char> start(std::max(b->grid, 1), 0);
+    for (int c = 0; c < b->grid; ++c) {
+        const double f = (c + 0.5) / b->grid * wt;
+        double acc = 0.0;
+        int v = 0;
+        for (; v < NBV - 1; ++v) {
+            acc += work[v];
+            if (f < acc && work[v] > 0) break;
+        }
+        while (work[v] == 0.0 && v > 0) --v;
+        start[c] = (unsigned char)v;
+    }
+    if (b->d_start) { cudaFree(b->d_start); b->d_start = nullptr; }
+    BCK(balloc(&b->d_start, start.size()));
+    BCK(cudaMemcpy(b->d_start, start.data(), start.size(), cudaMemcpyHostToDevice));
     b->policy = policy;
     return FE_OK;
 }
@@ -658,8 +688,11 @@ fe_status launch_jv(fe_batch *b, const float *vb, float *yb, bool with_skip, cud
 {
     const BatchInst *inst = b->d_inst + (with_skip ? 0 : b->count);
     const BatchFix *fix = b->d_fix + (with_skip ? 0 : b->count);
-    k_jv_batch<<<b->grid, BATCH_THREADS, b->smem, st>>>(inst, b->d_packs, b->npacks, vb, yb, b->d_err,
-                                                         b->d_counter);
+    Work W;
+    W.items = b->d_items;
+    for (int v = 0; v <= NBV; ++v) W.vbeg[v] = b->vbeg[v];
+    W.start = b->d_start;
+    k_jv_batch<<<b->grid, BATCH_THREADS, b->smem, st>>>(inst, W, vb, yb, b->d_err, b->d_counter);
     const unsigned fb = (unsigned)std::max<int64_t>(1, (b->nrows + 256 * FIX_ROWS - 1) / (256 * FIX_ROWS));
     k_fixup_batch<<<fb, 256, 0, st>>>(fix, b->d_row0, b->count, yb, b->d_counter);
     b->launches += 2;
@@ -700,8 +733,8 @@ fe_status build_tables(fe_batch *b)
     b->total = b->off[n];
     BCK(balloc(&b->d_err, 1));
     BCK(cudaMemset(b->d_err, 0, sizeof(int)));
-    BCK(balloc(&b->d_counter, 1));
-    BCK(cudaMemset(b->d_counter, 0, sizeof(unsigned)));
+    BCK(balloc(&b->d_counter, NBV));
+    BCK(cudaMemset(b->d_counter, 0, NBV * sizeof(unsigned)));
     BCK(balloc(&b->d_state, n));
     BCK(cudaMemset(b->d_state, 0, n * sizeof(CgState)));
     if (!b->h_state) BCK(cudaMallocHost(&b->h_state, n * sizeof(CgState)));
@@ -954,9 +987,10 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
             int bg = b->grid, bp = b->policy;
             std::vector<int> pols = o.policy >= 0 ? std::vector<int>{ o.policy } : std::vector<int>{ 0, 1, 2 };
             for (int pol : pols) {
-                if (s == FE_OK) s = upload_work(b, pol);
                 for (int m = 1; m <= per_sm_max && s == FE_OK; ++m) {
                     b->grid = m * b->num_sms;
+                    s = upload_work(b, pol);             // the CTAs' first variants depend on the grid
+                    if (s != FE_OK) break;
                     double ms = 0.0;
                     s = time_jv(b, 5, &ms);
                     if (s == FE_OK && ms < best) { best = ms; bg = b->grid; bp = pol; }
