@@ -110,6 +110,11 @@ fe_status fe_residual(fe_ctx *ctx, const double *u, double *r, void *stream);
  * d(d+1)/2 symmetric entries per point), plus the Jacobi diagonal of J.  u: device double[N_L]. */
 fe_status fe_linearize(fe_ctx *ctx, const double *u, void *stream);
 
+/* Device-side failures: every wait inside a kernel is bounded.  One that times out (a tile's
+ * tangent copy that does not land) abandons that kernel's work and sets the context's error word;
+ * the next synchronous call on the context (fe_jacobian_action_host, fe_cg_solve, newton_solve)
+ * returns FE_ERR_CUDA and clears the word. */
+
 /* fe_jacobian_action: y = J(u) v (Eq. 2).
  *   u == NULL : uses the quadrature-point Jacobian cached by the last fe_linearize (partial
  *               assembly); FE_ERR_STATE if there is none.

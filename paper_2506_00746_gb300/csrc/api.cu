@@ -234,6 +234,19 @@ void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
     c->fix.skip = nullptr;
 }
 
+// The device error word: a kernel whose bounded wait timed out has set it.  Synchronises st; on
+// an error resets the word and reports.
+fe_status check_device_error(fe_ctx *c, cudaStream_t st)
+{
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr == 0) return FE_OK;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    return fail(c, FE_ERR_CUDA, "a kernel's bounded wait timed out (code %d); results of that call are invalid", herr);
+}
+
 // CG on J x = b (x from 0) with the cached linearisation and preconditioner dinv, on c->own_stream.
 fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int precision, int batch, bool use_graph,
                  int *iters, int *done_code)
@@ -288,6 +301,10 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
         CK(cudaMemcpyAsync(h, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (h->done) break;
+    }
+    {
+        fe_status e = check_device_error(c, st);
+        if (e != FE_OK) return e;
     }
     if (precision == 32) {
         // the FP32 solution, unscaled, into the FP64 solution vector
@@ -690,8 +707,7 @@ extern "C" fe_status fe_jacobian_action_host(fe_ctx *c, const void *v_host, void
     s = apply_jv_cached(c, dv, dy, precision, st);
     if (s != FE_OK) return s;
     CK(cudaMemcpyAsync(y_host, dy, es * (size_t)c->nl, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return FE_OK;
+    return check_device_error(c, st);
 }
 
 extern "C" fe_status fe_jacobian_diagonal(fe_ctx *c, double *diag, void *stream)
