@@ -115,6 +115,12 @@ fe_status fe_linearize(fe_ctx *ctx, const double *u, void *stream);
  * the next synchronous call on the context (fe_jacobian_action_host, fe_cg_solve, newton_solve)
  * returns FE_ERR_CUDA and clears the word. */
 
+/* fe_selftest_wait_timeout: diagnostic of that path.  Runs one CTA whose bounded wait on an
+ * mbarrier phase that nothing completes (no arrival, no copy) gives up after about a second and
+ * sets the error word; returns FE_ERR_CUDA exactly as a real timeout would, with the word cleared
+ * and the context usable afterwards.  Synchronous on `stream`. */
+fe_status fe_selftest_wait_timeout(fe_ctx *ctx, void *stream);
+
 /* fe_jacobian_action: y = J(u) v (Eq. 2).
  *   u == NULL : uses the quadrature-point Jacobian cached by the last fe_linearize (partial
  *               assembly); FE_ERR_STATE if there is none.

@@ -98,6 +98,7 @@ _SIGS = {
     "fe_last_error": (c_char_p, [_CTX]),
     "fe_status_string": (c_char_p, [c_int]),
     "fe_element_matrices": (c_int, [_CTX, c_void_p, c_int, c_int64, c_int64, c_void_p, c_void_p]),
+    "fe_selftest_wait_timeout": (c_int, [_CTX, c_void_p]),
     "fe_batch_create": (c_int, [POINTER(fe_batch_item), c_int, POINTER(fe_batch_opts), POINTER(_BATCH)]),
     "fe_batch_info": (c_int, [_BATCH, c_int, POINTER(c_int64), POINTER(c_int64), POINTER(c_int)]),
     "fe_batch_shape": (c_int, [_BATCH, POINTER(c_int64), POINTER(c_int), POINTER(c_int), POINTER(c_int),
@@ -225,6 +226,10 @@ def fe_adjoint_vjp(ctx, u, lam, grad, stream=None):
 def fe_element_matrices(ctx, u, method: int, e0: int, count: int, K, stream=None):
     check(library().fe_element_matrices(ctx, ptr(u), method, e0, count, ptr(K), stream_handle(stream)),
           "fe_element_matrices", ctx)
+
+
+def fe_selftest_wait_timeout(ctx, stream=None):
+    check(library().fe_selftest_wait_timeout(ctx, stream_handle(stream)), "fe_selftest_wait_timeout", ctx)
 
 
 def fe_newton_default_opts() -> fe_newton_opts:

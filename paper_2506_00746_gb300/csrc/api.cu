@@ -710,6 +710,18 @@ extern "C" fe_status fe_jacobian_action_host(fe_ctx *c, const void *v_host, void
     return check_device_error(c, st);
 }
 
+extern "C" fe_status fe_selftest_wait_timeout(fe_ctx *c, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    {
+        LaunchScope ls(c, "wait_selftest", st);
+        k_wait_selftest<<<1, 32, 0, st>>>(c->d_err);
+    }
+    CKLAUNCH();
+    return check_device_error(c, st);
+}
+
 extern "C" fe_status fe_jacobian_diagonal(fe_ctx *c, double *diag, void *stream)
 {
     if (!c) return FE_ERR_ARG;

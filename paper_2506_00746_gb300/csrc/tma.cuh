@@ -2,6 +2,10 @@
 // shared-memory mbarriers, bounded mbarrier waits, and small cp.async copies.
 #pragma once
 
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
 namespace feod {
 
 // ---------------------------------------------------------------------------------------------

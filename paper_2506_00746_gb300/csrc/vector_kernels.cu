@@ -3,6 +3,7 @@
 // two-level tree, last-block finalisation) and fused CG updates whose scalars stay on the device.
 #include <cmath>
 
+#include "tma.cuh"
 #include "vector_kernels.h"
 
 namespace feod {
@@ -485,6 +486,20 @@ __global__ void k_cg_widen(double *__restrict__ y, const float *__restrict__ x, 
     const double sc = ldexp(1.0, st->scale_exp);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (double)x[i] * sc;
+}
+
+// Failure-path self-test: one CTA waits (bounded) on an mbarrier phase that nothing completes --
+// the arrival count is 1 and no thread arrives, no copy is issued -- so the wait gives up after
+// about a second and sets the error word as a timed-out tile would.  No fault, no trap.
+__global__ void k_wait_selftest(int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0) && threadIdx.x == 0) atomicExch(err, 4);
 }
 
 }  // namespace feod

@@ -149,3 +149,24 @@ def test_cg_solve_fp32_accuracy_and_scaling():
             assert its == it
             assert torch.equal(xs, x * 2.0 ** s)
     op.close()
+
+
+def test_device_wait_timeout_is_reported_and_context_survives():
+    """A bounded device wait that nothing completes gives up (about a second), the host reports
+    FE_ERR_CUDA, and the same context computes correctly afterwards."""
+    import torch
+    from paper_2506_00746_gb300 import FeodError, abi
+    w = I.Workload("3d_small", 3, 3, 2)
+    op, P, u0, ud = _setup(w)
+    with pytest.raises(FeodError) as ei:
+        abi.fe_selftest_wait_timeout(op.ctx)
+    assert ei.value.args and "FE_ERR_CUDA" in str(ei.value)
+    op.linearize(ud)
+    v = I.uniform_vector(op.n_dofs, seed=2)
+    y = op.jacobian_action(torch.from_numpy(v).cuda()).cpu().numpy()
+    y_ref = O.jv(P, u0, v)
+    assert np.linalg.norm(y - y_ref) <= 1e-12 * np.linalg.norm(y_ref)
+    # the word was cleared: a synchronous solve runs normally
+    u = ud.clone()
+    assert op.newton_solve(u, rtol=1e-8)["status"] == "FE_OK"
+    op.close()
