@@ -45,7 +45,8 @@ typedef enum {
     FE_OK = 0,
     FE_ERR_ARG = 1,            /* invalid argument (null pointer, size, range)               */
     FE_ERR_MESH = 2,           /* det J <= 0 at some quadrature point (inverted element)      */
-    FE_ERR_CUDA = 3,           /* a CUDA runtime call failed                                  */
+    FE_ERR_CUDA = 3,           /* a CUDA runtime call failed, or a kernel's bounded wait
+                                  timed out (see fe_selftest_wait_timeout)                    */
     FE_ERR_OOM = 4,            /* device or host allocation failed                           */
     FE_ERR_UNSUPPORTED = 5,    /* order / quadrature / size outside what is built            */
     FE_ERR_NAN = 6,            /* a NaN or Inf appeared in a norm                            */
@@ -79,7 +80,7 @@ typedef struct {
 typedef struct {
     int tile;                  /* elements per tile edge: one CTA owns tile^dim elements;
                                   0 = tuned default                                           */
-    int no_pipeline;           /* 1: apply the cached Jacobian with the per-element kernel
+    int per_element;           /* 1: apply the cached Jacobian with the per-element kernel
                                   (element-by-element sum factorisation, staged in-tile G^T)
                                   instead of the tile-level one (3D); for comparison only     */
 } fe_setup_opts;

@@ -32,7 +32,7 @@ class Operator:
 
     def __init__(self, dim: int, n: int, order: int, vertices, p: float = 3.0, eps: float = 0.0,
                  f_kind: int = 0, f_const: float = 1.0, rho=None, kappa_eps: float = 1e-3,
-                 kappa_q: float = 3.0, q1d: int = 0, tile: int = 0, pipeline: bool = True):
+                 kappa_q: float = 3.0, q1d: int = 0, tile: int = 0, tile_kernel: bool = True):
         import ctypes
 
         import torch
@@ -44,7 +44,7 @@ class Operator:
         prob = abi.fe_problem(p, eps, f_kind, f_const,
                               None if self._rho is None else self._rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                               kappa_eps, kappa_q)
-        opts = abi.fe_setup_opts(tile, 0 if pipeline else 1) if (tile or not pipeline) else None
+        opts = abi.fe_setup_opts(tile, 0 if tile_kernel else 1) if (tile or not tile_kernel) else None
         self.ctx = abi.fe_setup(mesh, order, q1d, prob, opts)
         self.dim, self.n, self.order, self.p = dim, n, order, p
         self.n_dofs, self.n_free = abi.fe_num_dofs(self.ctx)

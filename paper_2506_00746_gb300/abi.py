@@ -39,7 +39,7 @@ class fe_problem(ctypes.Structure):
 
 
 class fe_setup_opts(ctypes.Structure):
-    _fields_ = [("tile", c_int), ("no_pipeline", c_int)]
+    _fields_ = [("tile", c_int), ("per_element", c_int)]
 
 
 class fe_newton_opts(ctypes.Structure):

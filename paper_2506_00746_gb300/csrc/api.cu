@@ -374,7 +374,7 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     int smem_optin = 0;
     CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     c->smem_optin = smem_optin;
-    c->no_pipeline = opts && opts->no_pipeline;
+    c->per_element = opts && opts->per_element;
 
     c->ops = find_ops(dim, c->d1);
     if (!c->ops) return fail(c, FE_ERR_UNSUPPORTED, "no kernels built for dim %d order %d", dim, k);

@@ -848,7 +848,7 @@ fe_status setup_contexts(fe_batch *b, const fe_batch_item *items)
     for (int i = 0; i < b->count; ++i) {
         fe_setup_opts o{};
         o.tile = b->tile[i];
-        o.no_pipeline = 0;
+        o.per_element = 0;
         fe_status s = fe_setup_ex(items[i].mesh, items[i].order, 0, items[i].prob, &o, &b->ctx[i]);
         if (s != FE_OK) {
             char buf[64];

@@ -1057,7 +1057,7 @@ struct Ops {
         c->pipe_grid[variant<TC, TIO>()] = 0;
         if constexpr (DIM == 3) {
             constexpr int TT = max_tile(3, D1 - 1);
-            if (c->no_pipeline || c->T != TT) return cudaSuccess;
+            if (c->per_element || c->T != TT) return cudaSuccess;
             // FP32: the packed kernel k_jv_tile2; FP64: k_jv_tile
             const void *kern;
             size_t tsm;

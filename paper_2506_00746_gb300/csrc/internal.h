@@ -145,7 +145,7 @@ struct fe_ctx {
     // grid (= number of tiles) of the tile-level 3D J v kernel per variant [FP64, FP32, FP32 with
     // FP64 vectors]; 0 = that variant runs the per-element kernel
     int pipe_grid[3] = { 0, 0, 0 };
-    bool no_pipeline = false;
+    bool per_element = false;       // the cached J v uses the per-element kernel (comparison)
     int smem_optin = 0;
     int *h_err = nullptr;                       // pinned mirror of d_err
     int NQ = 0, NS = 0, NG = 0;                 // points per element, sym entries, geo comps

@@ -107,8 +107,9 @@ def test_tile_shapes_agree(tile):
 
 
 @pytest.mark.parametrize("n,k", [(7, 1), (5, 2), (6, 3), (3, 3), (4, 4), (3, 5), (2, 6)])
-def test_pipelined_and_simple_jacobian_kernels(n, k):
-    """The persistent TMA-pipelined J v and the one-CTA-per-tile J v both match the oracle."""
+def test_tile_and_per_element_jacobian_kernels(n, k):
+    """The tile-level J v (sum factorisation over the whole tile) and the per-element J v (per
+    element, staged in-tile G^T) both match the oracle."""
     import torch
     from paper_2506_00746_gb300 import Operator
     V = I.lattice_vertices(3, n, seed=0)
@@ -120,8 +121,8 @@ def test_pipelined_and_simple_jacobian_kernels(n, k):
     v32 = vd.float()
     y_ref32 = O.jv(P, u, v32.double().cpu().numpy())
     outs = []
-    for pipeline in (True, False):
-        op = Operator(3, n, k, V, p=3.0, pipeline=pipeline)
+    for tile_kernel in (True, False):
+        op = Operator(3, n, k, V, p=3.0, tile_kernel=tile_kernel)
         op.linearize(ud)
         y64 = op.jacobian_action(vd, precision=64).cpu().numpy()
         y32 = op.jacobian_action(v32, precision=32).double().cpu().numpy()
