@@ -680,12 +680,14 @@ def run_reference(args) -> dict | None:
     v = I.uniform_vector(P.n_dofs, seed=w.dir_seed)
     cores = O.set_threads(os.cpu_count() or 1)
     y = np.zeros(P.n_dofs)
-    # each step is the oracle J v over a bounded element sample, sized for ~1.5 s
+    # each step is the oracle J v over a bounded element sample, sized so that the whole run
+    # (warm-up and timed steps) takes about two minutes (at most 1.5 s per step)
+    per_step = min(1.5, 120.0 / max(args.steps + args.warmup, 1))
     m = max(1, P.n_elems // 1024)
     t0 = time.perf_counter()
     O.jv_partial(P, u, v, 0, m, y)
     dt = time.perf_counter() - t0
-    m = int(min(P.n_elems, max(m, m * 1.5 / max(dt, 1e-6))))
+    m = int(min(P.n_elems, max(m, m * per_step / max(dt, 1e-6))))
     for _ in range(args.warmup):
         O.jv_partial(P, u, v, 0, m, y)
     t0 = time.perf_counter()
