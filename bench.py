@@ -142,9 +142,14 @@ def jv_algorithmic_bytes(n_l: int, n_e: int, nq_per_elem: int, nl_per_elem: int,
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the Jacobian kernels: the kernel headers and the device
+    parameter blocks of internal.h (the host context that follows them does not enter)."""
     h = hashlib.sha256()
-    for f in ("element_kernels.cuh", "jv_tile.cuh", "tma.cuh", "internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2506_00746_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2506_00746_gb300", "csrc")
+    for f in ("element_kernels.cuh", "jv_tile.cuh", "tma.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    internal = open(os.path.join(csrc, "internal.h"), "rb").read()
+    h.update(internal.split(b"// The context.")[0])
     return h.hexdigest()[:16]
 
 
