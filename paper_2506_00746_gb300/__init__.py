@@ -136,7 +136,10 @@ class Operator:
     def newton_solve(self, u, rtol: float = 1e-8, inner_precision: int = 64, cg_rtol: float = 1e-4,
                      max_newton: int = 50, max_cg: int = 20000, line_search: bool = True,
                      cg_batch: int = 16, use_graph: bool = True, raise_on_error: bool = True, stream=None):
-        """Solve R(u) = 0 in place from u; returns a dict report."""
+        """Solve R(u) = 0 in place from u (Newton-CG, Jacobi-preconditioned, backtracking line search);
+        returns a dict report.  inner_precision: 64 (FP64 CG), -32 (FP32 J v inside an FP64 CG) or
+        32 (FP32 J v and FP32 CG vectors with compensated inner products); the residual, norms,
+        Newton update and line search are FP64 in every mode."""
         import torch
         self._chk(u, torch.float64, name="u")
         o = abi.fe_newton_default_opts()
@@ -157,6 +160,8 @@ class Operator:
         return out
 
     def cg_solve(self, b, rtol: float = 1e-10, max_iter: int = 50000, precision: int = 64, stream=None):
+        """Solve J x = b with the cached linearisation (x from 0); returns (x, iterations).
+        precision as newton_solve's inner_precision."""
         import torch
         x = self._vec()
         it = abi.fe_cg_solve(self.ctx, self._chk(b, torch.float64, name="b"), x, rtol, max_iter, precision, stream)

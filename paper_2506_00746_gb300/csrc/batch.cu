@@ -21,8 +21,8 @@ namespace feod {
 
 // ------------------------------------------------------------------------------------------------
 // tile variants of the batched launch, two tile edges per order 1..4; every variant's thread count
-// divides the CTA's 256 threads, so a CTA runs a pack of 256 / threads tiles at once, one per
-// thread group
+// divides the CTA's 256 threads, so a CTA working on a variant splits into 256 / threads
+// independent thread groups, one tile each
 // ------------------------------------------------------------------------------------------------
 constexpr int BATCH_MAX_ORDER = 4;
 constexpr int NBV = 8;
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(SEG_THREADS) k_bcg_direction32(float *__restri
         p[k] = __fmaf_rn(beta, p[k], __fmul_rn(dinv[k], r[k]));
 }
 
-// d = 2^e_i x (FP64), y = -r (FP64) helpers and the Jacobi scaling
+// d = 2^e_i x in FP64: instance i's FP32 CG solution of its scaled system, unscaled (exact)
 __global__ void __launch_bounds__(SEG_THREADS) k_bcg_widen(double *__restrict__ d, const float *__restrict__ x,
                                                            const Seg S, const CgState *st)
 {
@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(SEG_THREADS) k_bcg_widen(double *__restrict__ 
     for (int64_t k = S.lo[blockIdx.x] + threadIdx.x; k < S.hi[blockIdx.x]; k += SEG_THREADS) d[k] = (double)x[k] * sc;
 }
 
+// b = -R (the Newton right-hand sides) and the FP32 Jacobi scaling dinv = 1 / diag(J)
 __global__ void k_neg_recip(double *__restrict__ b, const double *__restrict__ r, float *__restrict__ dinv,
                             const double *__restrict__ diag, int64_t n)
 {
@@ -454,6 +455,7 @@ __global__ void k_neg_recip(double *__restrict__ b, const double *__restrict__ r
     }
 }
 
+// out = u + a d (a line-search trial point)
 __global__ void k_axpy_to(double *__restrict__ out, const double *__restrict__ u, double a,
                           const double *__restrict__ d, int64_t n)
 {
@@ -495,15 +497,12 @@ struct fe_batch {
     CgState *d_state = nullptr;
     CgState *h_state = nullptr;           // pinned
     double *d_partial = nullptr;
-    float *v32 = nullptr, *y32 = nullptr; // operands of fe_batch_jacobian_action (caller's)
     float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fq = nullptr, *dinv = nullptr;
     double *R = nullptr, *Rt = nullptr, *B = nullptr, *D = nullptr, *diag = nullptr;
     cudaStream_t st = nullptr;
     cudaGraphExec_t cg_exec = nullptr;
     int cg_batch = 0;
     int64_t launches = 0;
-    double tune_ms[NBV] = {};
-    std::string tune_note;
     std::string err;
 };
 
@@ -943,7 +942,6 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
             double ms = 0.0;
             if (s == FE_OK) s = time_jv(&one, 10, &ms);
             if (s == FE_OK && ms < best_ms) { best_ms = ms; chosen[k] = T; }
-            if (s == FE_OK) b->tune_ms[bv_of(k, T)] = ms;
             if (s != FE_OK && b->err.empty()) b->err = one.err;
             for (fe_ctx *c : one.ctx) fe_destroy(c);
             one.ctx.clear();
