@@ -204,7 +204,7 @@ fe_status fe_element_matrices(fe_ctx *ctx, const double *u, int method, int64_t 
 
 /* Newton-CG options.  Defaults (fe_newton_default_opts): rtol 1e-8, max_newton 50, max_cg 20000,
  * cg_rtol 1e-4, inner_precision 64, line_search 1, armijo 1e-4, max_halvings 20,
- * cg_batch 16, use_graph 1. */
+ * cg_batch 16, use_graph 2. */
 typedef struct {
     double rtol;               /* stop when ||R(u_k)||_2 <= rtol ||R(u_0)||_2                    */
     int max_newton;
@@ -215,8 +215,12 @@ typedef struct {
     int line_search;           /* 1: backtracking on ||R||_2                                   */
     double armijo;             /* accept alpha when ||R(u+alpha d)|| <= (1-armijo alpha)||R(u)|| */
     int max_halvings;
-    int cg_batch;              /* CG iterations enqueued between host convergence checks       */
-    int use_graph;             /* 1: replay each CG batch as a captured CUDA graph             */
+    int cg_batch;              /* CG iterations enqueued between host convergence checks
+                                  (use_graph 0, 1) or per pass of the device loop (2)          */
+    int use_graph;             /* 0: plain launches; 1: each CG batch replayed as a captured
+                                  CUDA graph, host check after each; 2: the whole CG solve as
+                                  one graph launch, a conditional WHILE node repeating the batch
+                                  while the device-side CG flag says running                   */
 } fe_newton_opts;
 
 #define FE_NEWTON_HIST 64
@@ -324,8 +328,10 @@ fe_status fe_batch_linearize(fe_batch *b, const double *u, void *stream);
 fe_status fe_batch_jacobian_action(fe_batch *b, const float *v, float *y, void *stream);
 /* Newton on every instance in lock step from u (device double batch vector, overwritten): per
  * step the FP64 residuals and FP32 tangents per instance, one Jacobi-preconditioned FP32 CG for
- * all instances (segmented reductions, per-instance flags; CG batches replayed as one captured
- * graph when opts->use_graph), per-instance FP64 line search.  opts->inner_precision is ignored
+ * all instances (segmented reductions, per-instance flags; with opts->use_graph 1 CG batches
+ * replayed as one captured graph with a host check after each, with 2 the whole CG as one graph
+ * launch whose conditional WHILE node repeats while any instance runs), per-instance FP64 line
+ * search.  opts->inner_precision is ignored
  * (FP32 CG, as newton_solve's 32).  reports: `count` per-instance reports or NULL; total: the
  * whole solve (max Newton steps, summed CG iterations, batch norms) or NULL.  Returns the first
  * failing instance's status, or FE_OK. */

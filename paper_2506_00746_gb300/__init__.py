@@ -135,7 +135,7 @@ class Operator:
     # -- solvers ----------------------------------------------------------------------------
     def newton_solve(self, u, rtol: float = 1e-8, inner_precision: int = 64, cg_rtol: float = 1e-4,
                      max_newton: int = 50, max_cg: int = 20000, line_search: bool = True,
-                     cg_batch: int = 16, use_graph: bool = True, raise_on_error: bool = True, stream=None):
+                     cg_batch: int = 16, use_graph: int = 2, raise_on_error: bool = True, stream=None):
         """Solve R(u) = 0 in place from u (Newton-CG, Jacobi-preconditioned, backtracking line search);
         returns a dict report.  inner_precision: 64 (FP64 CG), -32 (FP32 J v inside an FP64 CG) or
         32 (FP32 J v and FP32 CG vectors with compensated inner products); the residual, norms,
@@ -145,7 +145,7 @@ class Operator:
         o = abi.fe_newton_default_opts()
         o.rtol, o.inner_precision, o.cg_rtol = rtol, inner_precision, cg_rtol
         o.max_newton, o.max_cg, o.line_search = max_newton, max_cg, int(line_search)
-        o.cg_batch, o.use_graph = cg_batch, int(use_graph)
+        o.cg_batch, o.use_graph = cg_batch, int(use_graph)      # 0 plain, 1 graph batches, 2 device loop
         rep = abi.newton_solve(self.ctx, u, o, stream)
         out = {"status": abi.STATUS_NAMES.get(rep.status, rep.status), "newton_iters": rep.newton_iters,
                "cg_iters": rep.cg_iters_total, "halvings": rep.line_search_halvings, "r0": rep.r0,
@@ -275,7 +275,7 @@ class Batch:
         return y
 
     def newton_solve(self, u, rtol: float = 1e-8, cg_rtol: float = 1e-4, max_newton: int = 50,
-                     max_cg: int = 20000, cg_batch: int = 16, use_graph: bool = True, line_search: bool = True,
+                     max_cg: int = 20000, cg_batch: int = 16, use_graph: int = 2, line_search: bool = True,
                      raise_on_error: bool = True, stream=None):
         """Newton on every instance in lock step (FP32 CG, FP64 outer); returns (reports, total)."""
         import torch

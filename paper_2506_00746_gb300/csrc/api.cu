@@ -248,9 +248,12 @@ fe_status check_device_error(fe_ctx *c, cudaStream_t st)
 }
 
 // CG on J x = b (x from 0) with the cached linearisation and preconditioner dinv, on c->own_stream.
-fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int precision, int batch, bool use_graph,
+fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int precision, int batch, int graph_mode,
                  int *iters, int *done_code)
 {
+    // graph_mode: 0 plain launches, 1 captured batches with a host check after each, 2 the whole
+    // solve on the device (conditional WHILE node)
+    const bool use_graph = graph_mode != 0, device_loop = graph_mode == 2;
     cudaStream_t st = c->own_stream;
     CgState *s = cg_state(c);
     if (precision != 32) {
@@ -271,7 +274,7 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
     CKLAUNCH();
     if (batch < 1) batch = 1;
     const int gi = precision == 64 ? 0 : precision == -32 ? 1 : 2;
-    if (use_graph && (c->cg_exec[gi] == nullptr || c->cg_batch[gi] != batch)) {
+    if (use_graph && !device_loop && (c->cg_exec[gi] == nullptr || c->cg_batch[gi] != batch)) {
         if (c->cg_exec[gi]) { cudaGraphExecDestroy(c->cg_exec[gi]); c->cg_exec[gi] = nullptr; }
         const bool prof = c->prof;
         c->prof = false;
@@ -290,7 +293,49 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
         c->cg_batch[gi] = batch;
     }
     CgState *h = cg_host(c);
-    for (;;) {
+    if (use_graph && device_loop) {
+        // the whole solve as one graph launch: a conditional WHILE node whose body is `batch`
+        // iterations and the condition kernel; no host round trip until the solve ends
+        if (c->cg_loop_exec[gi] == nullptr || c->cg_loop_m[gi] != batch) {
+            if (c->cg_loop_exec[gi]) { cudaGraphExecDestroy(c->cg_loop_exec[gi]); c->cg_loop_exec[gi] = nullptr; }
+            cudaGraph_t g = nullptr;
+            CK(cudaGraphCreate(&g, 0));
+            cudaGraphConditionalHandle hc;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 1u, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams np = { cudaGraphNodeTypeConditional };   // aggregate: the rest zero
+            np.conditional.handle = hc;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+            if (e == cudaSuccess) {
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                const bool prof = c->prof;
+                c->prof = false;
+                const int64_t l0 = c->launches;
+                e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    enqueue_cg(c, batch, precision, st);
+                    k_cg_continue<<<1, 1, 0, st>>>(hc, s);
+                    e = cudaStreamEndCapture(st, &body);
+                }
+                c->prof = prof;
+                c->cg_launches[gi] = c->launches - l0;
+                c->launches = l0;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cg_loop_exec[gi], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(c, FE_ERR_CUDA, "device CG loop graph: %s", cudaGetErrorString(e));
+            c->cg_loop_m[gi] = batch;
+        }
+        CK(cudaGraphLaunch(c->cg_loop_exec[gi], st));
+        CK(cudaMemcpyAsync(h, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        // kernels run: `batch` iterations' launches (and the condition kernel) per body pass
+        const int64_t passes = std::max<int64_t>(1, (h->iter + batch - 1) / batch);
+        c->launches += passes * (c->cg_launches[gi] + 1);
+    }
+    for (; !(use_graph && device_loop);) {
         if (use_graph) {
             CK(cudaGraphLaunch(c->cg_exec[gi], st));
             c->launches += c->cg_launches[gi];
@@ -597,6 +642,8 @@ extern "C" void fe_destroy(fe_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
+    for (auto &g : c->cg_loop_exec)
+        if (g) cudaGraphExecDestroy(g);
     for (auto &g : c->cg_exec)
         if (g) cudaGraphExecDestroy(g);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -812,7 +859,7 @@ extern "C" fe_status fe_cg_solve(fe_ctx *c, const double *b, double *x, double r
     }
     CKLAUNCH();
     int it = 0, done = 0;
-    s = run_cg(c, b, rtol, max_iter, precision, 16, true, &it, &done);
+    s = run_cg(c, b, rtol, max_iter, precision, 16, 1, &it, &done);
     if (s != FE_OK) return s;
     CK(cudaMemcpyAsync(x, c->w_cx, (size_t)c->nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
@@ -835,7 +882,7 @@ extern "C" fe_status fe_newton_default_opts(fe_newton_opts *o)
     o->armijo = 1e-4;
     o->max_halvings = 20;
     o->cg_batch = 16;
-    o->use_graph = 1;
+    o->use_graph = 2;
     return FE_OK;
 }
 
@@ -891,7 +938,7 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
         CKLAUNCH();
         const auto c0 = std::chrono::steady_clock::now();
         int cg_it = 0, done = 0;
-        s = run_cg(c, c->w_d, o.cg_rtol, o.max_cg, jprec, o.cg_batch, o.use_graph != 0, &cg_it, &done);
+        s = run_cg(c, c->w_d, o.cg_rtol, o.max_cg, jprec, o.cg_batch, o.use_graph, &cg_it, &done);
         if (s != FE_OK) return s;
         cg_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c0).count();
         R.cg_iters_total += cg_it;

@@ -435,6 +435,16 @@ __global__ void __launch_bounds__(SEG_THREADS) k_bcg_direction32(float *__restri
         p[k] = __fmaf_rn(beta, p[k], __fmul_rn(dinv[k], r[k]));
 }
 
+// The condition of the device-side batched CG loop (a conditional WHILE node): repeat the body
+// while any instance's CG is running.  One warp; the body's kernels have finished when it runs.
+__global__ void k_bcg_continue(cudaGraphConditionalHandle h, const CgState *st, int count)
+{
+    int running = 0;
+    for (int i = threadIdx.x; i < count; i += 32) running |= st[i].done == 0;
+    running = __any_sync(0xffffffffu, running);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, running ? 1u : 0u);
+}
+
 // d = 2^e_i x in FP64: instance i's FP32 CG solution of its scaled system, unscaled (exact)
 __global__ void __launch_bounds__(SEG_THREADS) k_bcg_widen(double *__restrict__ d, const float *__restrict__ x,
                                                            const Seg S, const CgState *st)
@@ -500,8 +510,10 @@ struct fe_batch {
     float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fq = nullptr, *dinv = nullptr;
     double *R = nullptr, *Rt = nullptr, *B = nullptr, *D = nullptr, *diag = nullptr;
     cudaStream_t st = nullptr;
-    cudaGraphExec_t cg_exec = nullptr;
+    cudaGraphExec_t cg_exec = nullptr;    // one CG batch (use_graph 1)
     int cg_batch = 0;
+    cudaGraphExec_t cg_loop = nullptr;    // the whole CG on the device (use_graph 2)
+    int cg_loop_m = 0;
     int64_t launches = 0;
     std::string err;
 };
@@ -821,6 +833,7 @@ fe_status build_tables(fe_batch *b)
     for (int i = 0; i < n; ++i)
         BCK(cudaMemcpyToSymbol(c_bpairs, &b->ctx[i]->p32, sizeof(BasisPairs), (b->order[i] - 1) * sizeof(BasisPairs)));
     if (b->cg_exec) { cudaGraphExecDestroy(b->cg_exec); b->cg_exec = nullptr; }
+    if (b->cg_loop) { cudaGraphExecDestroy(b->cg_loop); b->cg_loop = nullptr; }
     // launch attributes and the resident CTAs per SM of this shape.  The shared-memory limit is
     // an attribute of the kernel for the whole process: raise it, never lower it below what an
     // earlier batch launches with.
@@ -1018,6 +1031,7 @@ extern "C" void fe_batch_destroy(fe_batch *b)
 {
     if (!b) return;
     if (b->cg_exec) cudaGraphExecDestroy(b->cg_exec);
+    if (b->cg_loop) cudaGraphExecDestroy(b->cg_loop);
     free_batch_device(b);
     if (b->h_state) cudaFreeHost(b->h_state);
     if (b->st) cudaStreamDestroy(b->st);
@@ -1158,7 +1172,32 @@ extern "C" fe_status fe_batch_newton_solve(fe_batch *b, double *u, const fe_newt
         // CG batches for all instances at once, replayed as one captured graph
         const auto c0 = std::chrono::steady_clock::now();
         const int m = std::max(1, o.cg_batch);
-        if (o.use_graph && (!b->cg_exec || b->cg_batch != m)) {
+        const bool device_loop = o.use_graph == 2;
+        if (device_loop && (!b->cg_loop || b->cg_loop_m != m)) {
+            // a conditional WHILE node around m iterations and the condition kernel
+            if (b->cg_loop) { cudaGraphExecDestroy(b->cg_loop); b->cg_loop = nullptr; }
+            const int64_t lsave = b->launches;
+            cudaGraph_t g = nullptr;
+            BCK(cudaGraphCreate(&g, 0));
+            cudaGraphConditionalHandle hc;
+            BCK(cudaGraphConditionalHandleCreate(&hc, g, 1u, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams np = { cudaGraphNodeTypeConditional };   // aggregate: the rest zero
+            np.conditional.handle = hc;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            BCK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            BCK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            enqueue_bcg(b, m, st);
+            k_bcg_continue<<<1, 32, 0, st>>>(hc, b->d_state, n);
+            BCK(cudaStreamEndCapture(st, &body));
+            BCK(cudaGraphInstantiate(&b->cg_loop, g, 0));
+            cudaGraphDestroy(g);
+            b->cg_loop_m = m;
+            b->launches = lsave;
+        }
+        if (o.use_graph == 1 && (!b->cg_exec || b->cg_batch != m)) {
             if (b->cg_exec) { cudaGraphExecDestroy(b->cg_exec); b->cg_exec = nullptr; }
             const int64_t lsave = b->launches;
             cudaGraph_t g = nullptr;
@@ -1170,7 +1209,15 @@ extern "C" fe_status fe_batch_newton_solve(fe_batch *b, double *u, const fe_newt
             b->cg_batch = m;
             b->launches = lsave;
         }
-        for (;;) {
+        if (device_loop) {
+            BCK(cudaGraphLaunch(b->cg_loop, st));
+            BCK(cudaMemcpyAsync(b->h_state, b->d_state, n * sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            BCK(cudaStreamSynchronize(st));
+            int maxit = 0;
+            for (int i = 0; i < n; ++i) maxit = std::max(maxit, b->h_state[i].iter);
+            b->launches += (int64_t)std::max(1, (maxit + m - 1) / m) * (5 * (int64_t)m + 1);
+        }
+        for (; !device_loop;) {
             if (o.use_graph) {
                 BCK(cudaGraphLaunch(b->cg_exec, st));
                 b->launches += 5 * (int64_t)m;

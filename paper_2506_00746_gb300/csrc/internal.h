@@ -187,6 +187,9 @@ struct fe_ctx {
     cudaGraphExec_t cg_exec[3] = { nullptr, nullptr, nullptr };
     int cg_batch[3] = { 0, 0, 0 };
     int64_t cg_launches[3] = { 0, 0, 0 };
+    // the device-side CG loop per precision: one conditional WHILE node around cg_loop_m iterations
+    cudaGraphExec_t cg_loop_exec[3] = { nullptr, nullptr, nullptr };
+    int cg_loop_m[3] = { 0, 0, 0 };
 
     feod::OpParams op{};
     feod::FixParams fix{};

@@ -502,4 +502,11 @@ __global__ void k_wait_selftest(int *err)
     if (!mbar_wait_bounded(&bar, 0) && threadIdx.x == 0) atomicExch(err, 4);
 }
 
+// The condition of the device-side CG loop (a conditional WHILE node): repeat the body while the
+// CG state is running.  One thread; the body's kernels have finished when it runs.
+__global__ void k_cg_continue(cudaGraphConditionalHandle h, const CgState *st)
+{
+    cudaGraphSetConditional(h, st->done == 0 ? 1u : 0u);
+}
+
 }  // namespace feod

@@ -55,6 +55,7 @@ __global__ void k_cg_update32(float *__restrict__ x, float *__restrict__ r, cons
 __global__ void k_cg_direction32(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ dinv,
                                  int64_t n, const CgState *st);
 __global__ void k_wait_selftest(int *err);
+__global__ void k_cg_continue(cudaGraphConditionalHandle h, const CgState *st);
 __global__ void k_cg_widen(double *__restrict__ y, const float *__restrict__ x, int64_t n, const CgState *st);
 
 }  // namespace feod

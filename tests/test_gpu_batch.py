@@ -95,11 +95,12 @@ def test_batch_newton_matches_oracle():
         ui = B.split(u)[i].cpu().numpy()
         assert np.linalg.norm(O.residual(P, ui)) <= 1e-8 * r0 * 1.01
     # graph replay and plain launches give bitwise the same iterates
-    a, b = B.concat(us), B.concat(us)
-    ra, _ = B.newton_solve(a, use_graph=True)
-    rb, _ = B.newton_solve(b, use_graph=False, cg_batch=3)
-    assert torch.equal(a, b)
-    assert [r["cg_iters"] for r in ra] == [r["cg_iters"] for r in rb]
+    a, b, c = B.concat(us), B.concat(us), B.concat(us)
+    ra, _ = B.newton_solve(a, use_graph=1)
+    rb, _ = B.newton_solve(b, use_graph=0, cg_batch=3)
+    rc, _ = B.newton_solve(c, use_graph=2, cg_batch=5)      # the whole CG as one graph launch
+    assert torch.equal(a, b) and torch.equal(a, c)
+    assert [r["cg_iters"] for r in ra] == [r["cg_iters"] for r in rb] == [r["cg_iters"] for r in rc]
     B.close()
 
 

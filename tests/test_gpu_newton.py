@@ -50,16 +50,18 @@ def test_newton_tight_matches_oracle(precision):
 
 
 def test_newton_graph_and_plain_launches_agree():
-    """Replaying CG batches as CUDA graphs gives bitwise the same iterates as plain launches."""
+    """Replaying CG batches as CUDA graphs, and the whole CG as one graph launch with a conditional
+    WHILE node, give bitwise the same iterates as plain launches."""
     import torch
     w = I.Workload("3d_small", 3, 3, 3)
     op, P, u0, ud = _setup(w)
-    for prec in (32, -32):
-        a, b = ud.clone(), ud.clone()
-        ra = op.newton_solve(a, inner_precision=prec, use_graph=True)
-        rb = op.newton_solve(b, inner_precision=prec, use_graph=False, cg_batch=5)
-        assert torch.equal(a, b)
-        assert ra["cg_hist"] == rb["cg_hist"]
+    for prec in (32, -32, 64):
+        a, b, c = ud.clone(), ud.clone(), ud.clone()
+        ra = op.newton_solve(a, inner_precision=prec, use_graph=1)
+        rb = op.newton_solve(b, inner_precision=prec, use_graph=0, cg_batch=5)
+        rc = op.newton_solve(c, inner_precision=prec, use_graph=2, cg_batch=3)    # device-side loop
+        assert torch.equal(a, b) and torch.equal(a, c)
+        assert ra["cg_hist"] == rb["cg_hist"] == rc["cg_hist"]
     op.close()
 
 
