@@ -302,7 +302,9 @@ def run_gpu(args) -> dict | None:
                                f"{nl} DOFs; step = one FP32 partially assembled J(u) v",
                    "n_dofs": nl, "n_elements": ne, "order": w.order, "p": w.p,
                    "l2": "inputs larger than L2 (FP32 tangent %.0f MB + index/vectors)" % (6 * 4 * ne * nq / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single GPU", "tile": None},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   # the library's default tile edge of 3D order k (elements per CTA = tile^3)
+                   "tile": {1: 4, 2: 3, 3: 2, 4: 2, 5: 2, 6: 1}[w.order]},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
