@@ -30,6 +30,8 @@ if ROOT not in sys.path:
 
 METRIC = "Jacobian action GDOF/s; Newton solve time to 1e-8 rel residual, FP64 vs mixed"
 WORKLOAD = "3d_p3_k3_64"
+# Newton modes (name, inner precision); fp64 last, the others are timed against it
+NEWTON_MODES = (("mixed", -32), ("mixed_fp32_cg", 32), ("double_float", 48), ("fp64", 64))
 
 
 # ------------------------------------------------------------------------------------------------
@@ -234,6 +236,11 @@ def run_gpu(args) -> dict | None:
     jv64 = lambda: op.jacobian_action(v64, precision=64, out=y64)
     t64, _ = timed(jv64, max(3, args.steps // 20), 2)
     n64 = max(3, args.steps // 20)
+    # double-float operator (FP32 word pairs): the first call splits the FP64 tangent, untimed
+    jvdf = lambda: op.jacobian_action(v64, precision=48, out=y64)
+    jvdf()
+    tdf, _ = timed(jvdf, max(3, args.steps // 10), 2)
+    ndf = max(3, args.steps // 10)
     jvcg = lambda: op.jacobian_action(v64, precision=-32, out=y64)
     tcg, _ = timed(jvcg, args.steps, 3)
     r = torch.empty_like(u0)
@@ -259,8 +266,9 @@ def run_gpu(args) -> dict | None:
     newton = {}
     if not args.no_newton:
         # mixed: FP32 J v inside an FP64 CG; mixed_fp32_cg: FP32 J v and FP32 CG vectors with
-        # compensated inner products; fp64: everything FP64
-        for name, prec in (("mixed", -32), ("mixed_fp32_cg", 32), ("fp64", 64)):
+        # compensated inner products; double_float: double-float J v inside an FP64 CG; fp64:
+        # everything FP64
+        for name, prec in NEWTON_MODES:
             u = u0.clone()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -272,7 +280,7 @@ def run_gpu(args) -> dict | None:
                             "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
                             "rel_residual": rep["rel"], "cg_time_s": round(rep["cg_ms"] / 1e3, 4),
                             "kernel_launches": rep["launches"]}
-        for name in ("mixed", "mixed_fp32_cg"):
+        for name, _ in NEWTON_MODES[:-1]:
             if "fp64" in newton and name in newton:
                 newton[f"speedup_{name}_vs_fp64"] = round(newton["fp64"]["time_s"] / newton[name]["time_s"], 3)
 
@@ -316,6 +324,7 @@ def run_gpu(args) -> dict | None:
         "e2e": {"value": round(e2e_value, 4), "unit": "GDOF/s", "h2d_bytes_per_step": 4 * nl,
                 "d2h_bytes_per_step": 4 * nl},
         "jv_f64_gdofs": round(nl * n64 / t64 / 1e9, 4),
+        "jv_double_float_gdofs": round(nl * ndf / tdf / 1e9, 4),
         "jv_cg_mixed_gdofs": round(nl * args.steps / tcg / 1e9, 4),
         "residual_f64_gdofs": round(nl * nres / tres / 1e9, 4),
         "newton": newton,
@@ -356,7 +365,7 @@ def _event_time(fn, steps: int, warmup: int) -> float:
 def _newton_modes(op, u0, max_newton: int) -> dict:
     import torch
     out = {}
-    for name, prec in (("mixed", -32), ("mixed_fp32_cg", 32), ("fp64", 64)):
+    for name, prec in NEWTON_MODES:
         u = u0.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -365,7 +374,7 @@ def _newton_modes(op, u0, max_newton: int) -> dict:
         out[name] = {"time_s": round(time.perf_counter() - t0, 4), "status": rep["status"],
                      "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
                      "rel_residual": rep["rel"]}
-    for name in ("mixed", "mixed_fp32_cg"):
+    for name, _ in NEWTON_MODES[:-1]:
         out[f"speedup_{name}_vs_fp64"] = round(out["fp64"]["time_s"] / out[name]["time_s"], 3)
     return out
 
@@ -400,6 +409,7 @@ def run_sweep(args) -> dict:
         kn, kms = prof.get("jv_pa_f32", (1, float("nan")))
         t_main = kms / 1e3 / max(kn, 1)
         t64 = _event_time(lambda: op.jacobian_action(v64, precision=64, out=y64), 5, 2)
+        tdf = _event_time(lambda: op.jacobian_action(v64, precision=48, out=y64), 10, 2)
         r = torch.empty_like(u0)
         tres = _event_time(lambda: op.residual(u0, out=r), 3, 1)
         b32 = jv_algorithmic_bytes(nl, ne, nq, nq, 4)
@@ -410,6 +420,7 @@ def run_sweep(args) -> dict:
                "jv_f32_hbm_frac": round(b32 / t_main / 1e9 / peaks["hbm_gbs"], 4),
                "jv_f64_gdofs": round(nl / t64 / 1e9, 3),
                "jv_f64_fp64_frac": round(fl / t64 / 1e12 / FP64_PEAK_TFLOPS, 4),
+               "jv_double_float_gdofs": round(nl / tdf / 1e9, 3),
                "residual_f64_gdofs": round(nl / tres / 1e9, 3)}
         if not args.no_newton:
             row["newton"] = _newton_modes(op, u0, args.max_newton)

@@ -128,6 +128,15 @@ fe_status fe_selftest_wait_timeout(fe_ctx *ctx, void *stream);
  *   u != NULL : stateless: recomputes J_D(u_q) . (B G P v) with one dual direction seeded by the
  *               gradient of v, nothing cached.
  *   precision : 64 -> v, y are double[N_L] and all arithmetic is FP64;
+ *               48 -> v, y are double[N_L]; double-float arithmetic: every value is the
+ *                     unevaluated sum of two FP32 words (a 48-bit significand, FP32's exponent
+ *                     range), computed on the FP32 pipes, from the FP64 tangent split into such
+ *                     pairs (split on the first call after each linearisation, into storage
+ *                     allocated on first use).  Each operation errs by a small multiple of 2^-48
+ *                     relative to its operands, as one FP64 operation does by 2^-53.  Entries of
+ *                     v, y and the tangent outside about [1e-30, 1e38] in magnitude lose
+ *                     precision to FP32's range.  Cached linearisation only: with u != NULL it
+ *                     returns FE_ERR_UNSUPPORTED;
  *               32 -> v, y are float[N_L], FP32 arithmetic and accumulation (the FP32 rounding of
  *                     the FP64 tangent when cached);
  *               -32 -> v, y are double[N_L] but the action is computed exactly as for 32 (the
@@ -143,7 +152,8 @@ fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host,
                                   void *stream);
 
 /* fe_jacobian_action_noalloc: the same y = J v as fe_jacobian_action with u == NULL (cached
- * linearisation, precision 64 / 32 / -32 with the same meaning), for callers that must not
+ * linearisation, precision 64 / 32 / -32 with the same meaning; not 48, whose tangent storage
+ * is allocated on first use), for callers that must not
  * allocate device memory while they run -- e.g. code executing while a stream capture in global
  * mode is active (cudaMalloc is not permitted there), or an application whose GPU memory is all
  * handed out by its own pool allocator, so that a cudaMalloc would fail or disturb the pool.
@@ -210,8 +220,9 @@ typedef struct {
     int max_newton;
     int max_cg;                /* per Newton step                                              */
     double cg_rtol;            /* inner CG stops when ||r_cg|| <= cg_rtol ||R(u_k)||           */
-    int inner_precision;       /* CG precision, as fe_jacobian_action's: 64 FP64; -32 FP32 J v
-                                  in an FP64 CG; 32 FP32 J v and FP32 CG vectors              */
+    int inner_precision;       /* CG precision, as fe_jacobian_action's: 64 FP64; 48 double-
+                                  float J v in an FP64 CG; -32 FP32 J v in an FP64 CG; 32
+                                  FP32 J v and FP32 CG vectors                                */
     int line_search;           /* 1: backtracking on ||R||_2                                   */
     double armijo;             /* accept alpha when ||R(u+alpha d)|| <= (1-armijo alpha)||R(u)|| */
     int max_halvings;
@@ -244,7 +255,8 @@ fe_status fe_newton_default_opts(fe_newton_opts *opts);
  * overwritten with the solution.  Each step: R and J_D at u (fused, FP64 dual numbers), Jacobi-
  * preconditioned CG on J d = -R with the partially assembled J, then a backtracking line search
  * on ||R|| (R, its norm, u and the line search always FP64).  inner_precision 64: the CG runs in
- * FP64.  -32: the FP32 operator (FP32 arithmetic on the FP32 rounding of the stored tangent) is
+ * FP64.  48: FP64 CG vectors and scalars with the double-float operator (the FP64 tangent split
+ * into FP32 word pairs before each CG), for -R scaled by a power of two near its RMS (exact).  -32: the FP32 operator (FP32 arithmetic on the FP32 rounding of the stored tangent) is
  * applied to FP64 CG vectors; dot products, norms and updates FP64.  32: the CG runs on FP32
  * vectors with the FP32 operator, for -R scaled by a power of two near its RMS (exact), with its
  * inner products accumulated in compensated FP32 (Ogita-Rump-Oishi Dot2) and summed in FP64; its
@@ -256,7 +268,7 @@ fe_status newton_solve(fe_ctx *ctx, double *u_inout, const fe_newton_opts *opts,
 
 /* fe_cg_solve: solve J x = b with the cached linearisation (e.g. the adjoint J lambda = F; J is
  * symmetric), x starting from 0, Jacobi-preconditioned CG to ||r|| <= rtol ||b||.  precision 64,
- * -32 or 32 as newton_solve's inner_precision (with 32 the attainable relative residual is about
+ * 48, -32 or 32 as newton_solve's inner_precision (with 32 the attainable relative residual is about
  * 1e-6, so a smaller rtol ends in FE_ERR_NOT_CONVERGED at max_iter).  b, x: device double[N_L].
  * Synchronous.  iters may be NULL. */
 fe_status fe_cg_solve(fe_ctx *ctx, const double *b, double *x, double rtol, int max_iter,

@@ -79,8 +79,9 @@ class Operator:
     def jacobian_action(self, v, u=None, precision: int = 64, out=None, stream=None):
         """J(u) v: cached linearisation when u is None, else stateless (dual seeded by grad v).
 
-        precision 64 (double v/y), 32 (float v/y, FP32 arithmetic) or -32 (double v/y, FP32
-        arithmetic)."""
+        precision 64 (double v/y), 48 (double v/y, double-float arithmetic: FP32 word pairs on
+        the FP32 pipes, about 48 significant bits; cached linearisation only), 32 (float v/y, FP32
+        arithmetic) or -32 (double v/y, FP32 arithmetic)."""
         import torch
         io = torch.float32 if precision == 32 else torch.float64
         self._chk(v, io, name="v")
@@ -137,9 +138,10 @@ class Operator:
                      max_newton: int = 50, max_cg: int = 20000, line_search: bool = True,
                      cg_batch: int = 16, use_graph: int = 2, raise_on_error: bool = True, stream=None):
         """Solve R(u) = 0 in place from u (Newton-CG, Jacobi-preconditioned, backtracking line search);
-        returns a dict report.  inner_precision: 64 (FP64 CG), -32 (FP32 J v inside an FP64 CG) or
-        32 (FP32 J v and FP32 CG vectors with compensated inner products); the residual, norms,
-        Newton update and line search are FP64 in every mode."""
+        returns a dict report.  inner_precision: 64 (FP64 CG), 48 (double-float J v inside an FP64
+        CG), -32 (FP32 J v inside an FP64 CG) or 32 (FP32 J v and FP32 CG vectors with compensated
+        inner products); the residual, norms, Newton update and line search are FP64 in every
+        mode."""
         import torch
         self._chk(u, torch.float64, name="u")
         o = abi.fe_newton_default_opts()

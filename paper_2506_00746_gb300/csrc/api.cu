@@ -174,6 +174,23 @@ fe_status ensure_tangent(fe_ctx *c, bool f64, bool f32)
     return FE_OK;
 }
 
+// The double-float tangent: allocated on first use, split from the FP64 tangent when that has
+// changed since (stream-ordered on st).
+fe_status prepare_tangent_df(fe_ctx *c, cudaStream_t st)
+{
+    if (c->lindf) return FE_OK;
+    if (!c->lin64) return fail(c, FE_ERR_STATE, "no FP64 linearisation cached (call fe_linearize)");
+    const size_t n64 = (size_t)c->ntiles * c->tqs64;
+    if (!c->d_Tdf) CK(dalloc(c, &c->d_Tdf, n64));
+    {
+        LaunchScope ls(c, "split_df", st);
+        k_split_df<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->d_T64, c->d_Tdf, (int64_t)n64);
+    }
+    CKLAUNCH();
+    c->lindf = true;
+    return FE_OK;
+}
+
 // deterministic dot product, synchronous on stream st
 fe_status dot_sync(fe_ctx *c, const double *a, const double *b, double *out, cudaStream_t st)
 {
@@ -200,16 +217,21 @@ fe_status apply_jv_cached(fe_ctx *c, const void *v, void *y, int precision, cuda
     } else if (precision == -32) {
         if (!c->lin32) return fail(c, FE_ERR_STATE, "no FP32 linearisation cached (call fe_linearize)");
         c->ops->jv_pa_32d(c, (const double *)v, (double *)y, st);
+    } else if (precision == 48) {
+        fe_status s = prepare_tangent_df(c, st);
+        if (s != FE_OK) return s;
+        c->ops->jv_pa_df(c, (const double *)v, (double *)y, st);
     } else {
-        return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
+        return fail(c, FE_ERR_ARG, "precision must be 64, 48, 32 or -32");
     }
     CKLAUNCH();
     return FE_OK;
 }
 
 // Enqueue `m` CG iterations (J p, alpha, update, direction); every kernel is a no-op once the
-// device flag `done` is set.  precision 64: FP64 operator and vectors; -32: FP32 operator, FP64
-// vectors; 32: FP32 operator and vectors (CG scalars and inner-product sums in FP64).
+// device flag `done` is set.  precision 64: FP64 operator and vectors; 48: double-float operator,
+// FP64 vectors; -32: FP32 operator, FP64 vectors; 32: FP32 operator and vectors (CG scalars and
+// inner-product sums in FP64).
 void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
 {
     CgState *s = cg_state(c);
@@ -219,6 +241,7 @@ void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
     for (int i = 0; i < m; ++i) {
         if (precision != 32) {
             if (precision == 64) c->ops->jv_pa_64(c, c->w_cp, c->w_cq, st);
+            else if (precision == 48) c->ops->jv_pa_df(c, c->w_cp, c->w_cq, st);
             else c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
             { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
             { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv, n, s, c->w_partial); }
@@ -256,7 +279,22 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
     const bool use_graph = graph_mode != 0, device_loop = graph_mode == 2;
     cudaStream_t st = c->own_stream;
     CgState *s = cg_state(c);
-    if (precision != 32) {
+    if (precision == 48) {
+        // solve for b / 2^e (2^e near the RMS of b), staged in q (first written by J p)
+        CgState *ds = s + 1;
+        {
+            LaunchScope ls(c, "dot", st);
+            k_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, b, c->nl, c->w_partial + 2 * RED_BLOCKS, &ds->counter,
+                                                      &ds->scalar);
+        }
+        {
+            LaunchScope ls(c, "scale_rhs", st);
+            k_scale_rhs<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cq, b, c->nl, &ds->scalar, s);
+        }
+        LaunchScope ls(c, "cg_init", st);
+        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cq, c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->nl, s,
+                                                      rtol, max_iter, c->w_partial);
+    } else if (precision != 32) {
         LaunchScope ls(c, "cg_init", st);
         k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->nl, s, rtol,
                                                       max_iter, c->w_partial);
@@ -273,7 +311,7 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
     }
     CKLAUNCH();
     if (batch < 1) batch = 1;
-    const int gi = precision == 64 ? 0 : precision == -32 ? 1 : 2;
+    const int gi = precision == 64 ? 0 : precision == -32 ? 1 : precision == 32 ? 2 : 3;
     if (use_graph && !device_loop && (c->cg_exec[gi] == nullptr || c->cg_batch[gi] != batch)) {
         if (c->cg_exec[gi]) { cudaGraphExecDestroy(c->cg_exec[gi]); c->cg_exec[gi] = nullptr; }
         const bool prof = c->prof;
@@ -355,6 +393,9 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
         // the FP32 solution, unscaled, into the FP64 solution vector
         LaunchScope ls(c, "cg_widen", st);
         k_cg_widen<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cx, c->w_fx, c->nl, s);
+    } else if (precision == 48) {
+        LaunchScope ls(c, "unscale", st);
+        k_unscale<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cx, c->nl, s);
     }
     CKLAUNCH();
     if (iters) *iters = h->iter;
@@ -537,6 +578,8 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
             c->p32.BG[i] = make_float2((float)B, (float)G);
             c->p32.GB[i] = make_float2((float)G, (float)B);
             c->p32.BB[i] = make_float2((float)B, (float)B);
+            c->bdf.B[i] = dfloat(B); c->bdf.G[i] = dfloat(G); c->bdf.B2[i] = dfloat(B * B);
+            c->bdf.G2[i] = dfloat(G * G); c->bdf.BG[i] = dfloat(B * G);
         }
     c->gp.dim = dim; c->gp.d1 = c->d1; c->gp.q1 = c->q1; c->gp.n = n; c->gp.T = T; c->gp.nt = c->nt;
     c->gp.nepad = c->nepad; c->gp.f_kind = prob->f_kind; c->gp.f_const = prob->f_const; c->gp.p = prob->p;
@@ -637,7 +680,7 @@ extern "C" void fe_destroy(fe_ctx *c)
 {
     if (!c) return;
     void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_fix_off, c->d_hdst, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
-                     c->d_dkr, c->d_T64, c->d_T32, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
+                     c->d_dkr, c->d_T64, c->d_T32, c->d_Tdf, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
                      c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_fx, c->w_fr, c->w_fp, c->w_fq, c->w_state, c->w_partial };
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -721,6 +764,7 @@ extern "C" fe_status fe_linearize(fe_ctx *c, const double *u, void *stream)
     c->ops->diag_64(c, c->d_diag, st);
     CKLAUNCH();
     c->lin64 = c->lin32 = c->have_diag = true;
+    c->lindf = false;
     return FE_OK;
 }
 
@@ -734,7 +778,9 @@ extern "C" fe_status fe_jacobian_action(fe_ctx *c, const double *u, const void *
     if (precision == 64) c->ops->jv_dual_64(c, u, (const double *)v, (double *)y, st);
     else if (precision == 32) c->ops->jv_dual_32(c, u, (const float *)v, (float *)y, st);
     else if (precision == -32) c->ops->jv_dual_32d(c, u, (const double *)v, (double *)y, st);
-    else return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
+    else if (precision == 48)
+        return fail(c, FE_ERR_UNSUPPORTED, "precision 48 applies to the cached linearisation only (u = NULL)");
+    else return fail(c, FE_ERR_ARG, "precision must be 64, 48, 32 or -32");
     CKLAUNCH();
     return FE_OK;
 }
@@ -823,7 +869,7 @@ extern "C" fe_status fe_set_design(fe_ctx *c, const double *rho, void *stream)
                                                                             c->kappa_q, c->d_kr, c->d_dkr);
     }
     CKLAUNCH();
-    c->lin64 = c->lin32 = c->have_diag = false;
+    c->lin64 = c->lin32 = c->have_diag = c->lindf = false;
     return FE_OK;
 }
 
@@ -845,14 +891,16 @@ extern "C" fe_status fe_cg_solve(fe_ctx *c, const double *b, double *x, double r
 {
     if (!c) return FE_ERR_ARG;
     if (!b || !x || b == x) return fail(c, FE_ERR_ARG, "fe_cg_solve: null or aliased vectors");
-    if (precision != 64 && precision != 32 && precision != -32)
-        return fail(c, FE_ERR_ARG, "precision must be 64, 32 or -32");
-    if ((precision == 64 && !c->lin64) || (precision != 64 && !c->lin32) || !c->have_diag)
+    if (precision != 64 && precision != 48 && precision != 32 && precision != -32)
+        return fail(c, FE_ERR_ARG, "precision must be 64, 48, 32 or -32");
+    const bool f64 = precision == 64 || precision == 48;
+    if ((f64 && !c->lin64) || (!f64 && !c->lin32) || !c->have_diag)
         return fail(c, FE_ERR_STATE, "no linearisation cached (call fe_linearize)");
     fe_status s = ensure_work(c);
     if (s != FE_OK) return s;
     CK(cudaStreamSynchronize(as_stream(stream)));
     cudaStream_t st = c->own_stream;
+    if (precision == 48 && (s = prepare_tangent_df(c, st)) != FE_OK) return s;
     {
         LaunchScope ls(c, "reciprocal", st);
         k_reciprocal<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_dinv, c->d_diag, c->nl);
@@ -893,11 +941,13 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
     if (!u) return fail(c, FE_ERR_ARG, "newton_solve: null u");
     fe_newton_opts o;
     if (opts_in) o = *opts_in; else fe_newton_default_opts(&o);
-    if (o.inner_precision != 64 && o.inner_precision != 32 && o.inner_precision != -32)
-        return fail(c, FE_ERR_ARG, "inner_precision must be 64, 32 or -32");
+    if (o.inner_precision != 64 && o.inner_precision != 48 && o.inner_precision != 32 && o.inner_precision != -32)
+        return fail(c, FE_ERR_ARG, "inner_precision must be 64, 48, 32 or -32");
     fe_newton_report R;
     std::memset(&R, 0, sizeof R);
-    const bool mixed = o.inner_precision != 64;
+    // FP32 tangent for the FP32 operators; the FP64 one (split into FP32 word pairs before each CG
+    // in mode 48) otherwise
+    const bool mixed = o.inner_precision == 32 || o.inner_precision == -32;
     fe_status s = ensure_work(c);
     if (s == FE_OK) s = ensure_tangent(c, !mixed, mixed);
     if (s != FE_OK) return s;
@@ -936,6 +986,12 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
             k_scale<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_d, c->w_r, -1.0, c->nl);
         }
         CKLAUNCH();
+        if (jprec == 48) {
+            c->lin64 = true;
+            c->lindf = false;
+            s = prepare_tangent_df(c, st);
+            if (s != FE_OK) return s;
+        }
         const auto c0 = std::chrono::steady_clock::now();
         int cg_it = 0, done = 0;
         s = run_cg(c, c->w_d, o.cg_rtol, o.max_cg, jprec, o.cg_batch, o.use_graph, &cg_it, &done);
@@ -973,7 +1029,7 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
         ++it;
     }
     CK(cudaStreamSynchronize(st));
-    c->lin64 = !mixed; c->lin32 = mixed; c->have_diag = false;
+    c->lin64 = !mixed; c->lin32 = mixed; c->have_diag = false; c->lindf = false;
     R.newton_iters = it;
     R.r_final = rnorm;
     R.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -1013,9 +1013,10 @@ struct Ops {
         const size_t sm = smem_bytes<DIM, D1>(c->S, c->T, sizeof(TC), 1);
         const TC *Tq;
         const BasisT<TC> *bs;
-        if constexpr (sizeof(TC) == 8) { Tq = reinterpret_cast<const TC *>(c->d_T64); bs = reinterpret_cast<const BasisT<TC> *>(&c->b64); }
-        else { Tq = reinterpret_cast<const TC *>(c->d_T32); bs = reinterpret_cast<const BasisT<TC> *>(&c->b32); }
-        const char *name = sizeof(TC) == 8 ? "jv_pa_f64" : "jv_pa_f32";
+        const char *name;
+        if constexpr (is_dfloat<TC>::value) { Tq = c->d_Tdf; bs = &c->bdf; name = "jv_pa_df"; }
+        else if constexpr (sizeof(TC) == 8) { Tq = c->d_T64; bs = &c->b64; name = "jv_pa_f64"; }
+        else { Tq = c->d_T32; bs = &c->b32; name = "jv_pa_f32"; }
         if constexpr (DIM == 3) {
             const int grid = c->pipe_grid[variant<TC, TIO>()];
             if (grid > 0) {
@@ -1047,7 +1048,10 @@ struct Ops {
 
     // index of the (compute, I/O) variant in fe_ctx::pipe_grid
     template <typename TC, typename TIO>
-    static constexpr int variant() { return sizeof(TC) == 8 ? 0 : (sizeof(TIO) == 4 ? 1 : 2); }
+    static constexpr int variant()
+    {
+        return is_dfloat<TC>::value ? 3 : sizeof(TC) == 8 ? 0 : (sizeof(TIO) == 4 ? 1 : 2);
+    }
 
     // Enable the tile-level kernel of one variant when the context uses the compiled tile edge and
     // its shared memory and registers fit; otherwise the per-element kernel applies J.
@@ -1058,7 +1062,7 @@ struct Ops {
         if constexpr (DIM == 3) {
             constexpr int TT = max_tile(3, D1 - 1);
             if (c->per_element || c->T != TT) return cudaSuccess;
-            // FP32: the packed kernel k_jv_tile2; FP64: k_jv_tile
+            // FP32: the packed kernel k_jv_tile2; FP64 and double-float: k_jv_tile
             const void *kern;
             size_t tsm;
             if constexpr (sizeof(TC) == 4) {
@@ -1086,6 +1090,7 @@ struct Ops {
     static void jv_pa_64(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<double, double>(c, v, y, st); }
     static void jv_pa_32(fe_ctx *c, const float *v, float *y, cudaStream_t st) { jv_pa<float, float>(c, v, y, st); }
     static void jv_pa_32d(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<float, double>(c, v, y, st); }
+    static void jv_pa_df(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<dfloat, double>(c, v, y, st); }
 
     template <typename TC, typename TIO>
     static void jv_dual(fe_ctx *c, const double *u, const TIO *v, TIO *y, cudaStream_t st)
@@ -1152,6 +1157,7 @@ struct Ops {
         FEOD_RAISE((k_jv_pa<DIM, D1, double, double>), s1d);
         FEOD_RAISE((k_jv_pa<DIM, D1, float, float>), s1f);
         FEOD_RAISE((k_jv_pa<DIM, D1, float, double>), s1f);
+        FEOD_RAISE((k_jv_pa<DIM, D1, dfloat, double>), s1d);
         FEOD_RAISE((k_jv_dual<DIM, D1, double, double>), s2d);
         FEOD_RAISE((k_jv_dual<DIM, D1, float, float>), s2f);
         FEOD_RAISE((k_jv_dual<DIM, D1, float, double>), s2f);
@@ -1163,6 +1169,7 @@ struct Ops {
         if ((e = prepare_tile<double, double>(c)) != cudaSuccess) return e;
         if ((e = prepare_tile<float, float>(c)) != cudaSuccess) return e;
         if ((e = prepare_tile<float, double>(c)) != cudaSuccess) return e;
+        if ((e = prepare_tile<dfloat, double>(c)) != cudaSuccess) return e;
         // the two FP32 variants must run the same kernel (the FP64-vector one is defined to give
         // exactly the FP32 result): use the tile kernel for both or for neither
         if (c->pipe_grid[1] == 0 || c->pipe_grid[2] == 0) c->pipe_grid[1] = c->pipe_grid[2] = 0;
@@ -1171,7 +1178,7 @@ struct Ops {
 
     static const OpTable *table()
     {
-        static const OpTable t = { DIM, D1, residual, jv_pa_64, jv_pa_32, jv_pa_32d,
+        static const OpTable t = { DIM, D1, residual, jv_pa_64, jv_pa_32, jv_pa_32d, jv_pa_df,
                                    jv_dual_64, jv_dual_32, jv_dual_32d, diag_64, diag_32, vjp,
                                    prepare, max_smem };
         return &t;

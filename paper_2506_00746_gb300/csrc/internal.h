@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/feod.h"
+#include "dfloat.cuh"
 
 namespace feod {
 
@@ -115,6 +116,8 @@ struct OpTable {
     void (*jv_pa_64)(fe_ctx *c, const double *v, double *y, cudaStream_t st);
     void (*jv_pa_32)(fe_ctx *c, const float *v, float *y, cudaStream_t st);
     void (*jv_pa_32d)(fe_ctx *c, const double *v, double *y, cudaStream_t st);
+    // double-float operator (FP32 word pairs) with FP64 vectors, from the double-float tangent
+    void (*jv_pa_df)(fe_ctx *c, const double *v, double *y, cudaStream_t st);
     // stateless J(u) v with one dual direction
     void (*jv_dual_64)(fe_ctx *c, const double *u, const double *v, double *y, cudaStream_t st);
     void (*jv_dual_32)(fe_ctx *c, const double *u, const float *v, float *y, cudaStream_t st);
@@ -143,8 +146,8 @@ struct fe_ctx {
     int64_t tqs32 = 0, tqs64 = 0;               // per-tile tangent strides (elements)
     uint16_t *d_gt_off = nullptr, *d_gt_src = nullptr;   // in-tile G^T table
     // grid (= number of tiles) of the tile-level 3D J v kernel per variant [FP64, FP32, FP32 with
-    // FP64 vectors]; 0 = that variant runs the per-element kernel
-    int pipe_grid[3] = { 0, 0, 0 };
+    // FP64 vectors, double-float with FP64 vectors]; 0 = that variant runs the per-element kernel
+    int pipe_grid[4] = { 0, 0, 0, 0 };
     bool per_element = false;       // the cached J v uses the per-element kernel (comparison)
     int smem_optin = 0;
     int *h_err = nullptr;                       // pinned mirror of d_err
@@ -168,10 +171,12 @@ struct fe_ctx {
     double *d_kr = nullptr, *d_dkr = nullptr;   // internal order
     double *d_T64 = nullptr;
     float *d_T32 = nullptr;
+    feod::dfloat *d_Tdf = nullptr;  // double-float copy of the FP64 tangent (allocated on first use)
     double *d_diag = nullptr;
     void *d_halo = nullptr;       // nfixh * 8 bytes: cross-tile partial sums in fix-up order
     int *d_err = nullptr;
     bool lin64 = false, lin32 = false, have_diag = false;
+    bool lindf = false;           // d_Tdf holds the current FP64 tangent
 
     // Newton / CG work space (allocated on first use)
     double *w_r = nullptr, *w_d = nullptr, *w_trial = nullptr;
@@ -183,18 +188,19 @@ struct fe_ctx {
     void *h_state = nullptr;      // pinned host mirror
     cudaStream_t own_stream = nullptr;
     // captured CG batches: [0] FP64 operator and vectors, [1] FP32 operator with FP64 vectors,
-    // [2] FP32 operator and vectors
-    cudaGraphExec_t cg_exec[3] = { nullptr, nullptr, nullptr };
-    int cg_batch[3] = { 0, 0, 0 };
-    int64_t cg_launches[3] = { 0, 0, 0 };
+    // [2] FP32 operator and vectors, [3] double-float operator with FP64 vectors
+    cudaGraphExec_t cg_exec[4] = { nullptr, nullptr, nullptr, nullptr };
+    int cg_batch[4] = { 0, 0, 0, 0 };
+    int64_t cg_launches[4] = { 0, 0, 0, 0 };
     // the device-side CG loop per precision: one conditional WHILE node around cg_loop_m iterations
-    cudaGraphExec_t cg_loop_exec[3] = { nullptr, nullptr, nullptr };
-    int cg_loop_m[3] = { 0, 0, 0 };
+    cudaGraphExec_t cg_loop_exec[4] = { nullptr, nullptr, nullptr, nullptr };
+    int cg_loop_m[4] = { 0, 0, 0, 0 };
 
     feod::OpParams op{};
     feod::FixParams fix{};
     feod::BasisT<double> b64{};
     feod::BasisT<float> b32{};
+    feod::BasisT<feod::dfloat> bdf{};
     feod::BasisPairs p32{};
     feod::GeomParams gp{};
     const feod::OpTable *ops = nullptr;

@@ -60,7 +60,7 @@ __host__ __device__ inline size_t tile_smem_bytes(int64_t tqs, int /*Spad*/)
 }
 
 // n consecutive shared-memory values into registers; 16-byte vector loads when n % 4 == 0 (FP32)
-// or n % 2 == 0 (FP64) -- the caller guarantees the alignment in those cases.
+// or n % 2 == 0 (8-byte types: FP64, double-float) -- the caller guarantees the alignment then.
 template <int N, typename TC>
 __device__ __forceinline__ void lds_run(const TC *p, TC (&r)[N])
 {
@@ -71,10 +71,11 @@ __device__ __forceinline__ void lds_run(const TC *p, TC (&r)[N])
             r[i] = w.x; r[i + 1] = w.y; r[i + 2] = w.z; r[i + 3] = w.w;
         }
     } else if constexpr (sizeof(TC) == 8 && N % 2 == 0) {
+        struct alignas(16) Two { TC a, b; };
 #pragma unroll
         for (int i = 0; i < N; i += 2) {
-            const double2 w = *reinterpret_cast<const double2 *>(p + i);
-            r[i] = w.x; r[i + 1] = w.y;
+            const Two w = *reinterpret_cast<const Two *>(p + i);
+            r[i] = w.a; r[i + 1] = w.b;
         }
     } else {
 #pragma unroll

@@ -315,6 +315,14 @@ __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, do
         y[i] = alpha * x[i];
 }
 
+// Double-float copy of an FP64 array: x -> (fl32(x), fl32(x - fl32(x))), relative error <= 2^-48
+// (for |x| inside FP32's normal range)
+__global__ void k_split_df(const double *__restrict__ x, dfloat *__restrict__ y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = dfloat(x[i]);
+}
+
 // y = 1 / x rounded to FP32 (Jacobi preconditioner from the assembled diagonal)
 __global__ void k_reciprocal(float *__restrict__ y, const double *__restrict__ x, int64_t n)
 {
@@ -478,6 +486,27 @@ __global__ void k_cg_direction32(float *__restrict__ p, const float *__restrict_
         p4[i] = pv;
     }
     for (int64_t i = 4 * I.n4 + I.g0; i < n; i += I.gs) p[i] = __fmaf_rn(beta, p[i], __fmul_rn(dinv[i], r[i]));
+}
+
+// Double-float CG (FP64 vectors): y = b / 2^e with e = cg_scale_exp(*bb, n), recorded in the CG
+// state (exact).  The operator converts its FP64 input to FP32 word pairs, so the scaled system
+// keeps the pairs' low words far from the FP32 underflow threshold.
+__global__ void k_scale_rhs(double *__restrict__ y, const double *__restrict__ b, int64_t n, const double *bb,
+                            CgState *st)
+{
+    const int e = cg_scale_exp(*bb, n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->scale_exp = e;
+    const double sc = ldexp(1.0, -e);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = b[i] * sc;
+}
+
+// x = 2^e x in place: the solution of the unscaled system (exact)
+__global__ void k_unscale(double *__restrict__ x, int64_t n, const CgState *st)
+{
+    const double sc = ldexp(1.0, st->scale_exp);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= sc;
 }
 
 // y = 2^e x in FP64 (the FP32 CG solution of the unscaled system; exact)

@@ -44,6 +44,7 @@ __global__ void k_waxpy(double *__restrict__ y, const double *__restrict__ a, do
                         const double *__restrict__ b, int64_t n);
 __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, double alpha, int64_t n);
 __global__ void k_reciprocal(float *__restrict__ y, const double *__restrict__ x, int64_t n);
+__global__ void k_split_df(const double *__restrict__ x, dfloat *__restrict__ y, int64_t n);
 __global__ void k_cg_init32(const double *__restrict__ b, const float *__restrict__ dinv, float *__restrict__ x,
                             float *__restrict__ r, float *__restrict__ p, int64_t n, CgState *st, const double *bb,
                             double rtol, int max_iter, double *partial);
@@ -56,6 +57,9 @@ __global__ void k_cg_direction32(float *__restrict__ p, const float *__restrict_
                                  int64_t n, const CgState *st);
 __global__ void k_wait_selftest(int *err);
 __global__ void k_cg_continue(cudaGraphConditionalHandle h, const CgState *st);
+__global__ void k_scale_rhs(double *__restrict__ y, const double *__restrict__ b, int64_t n, const double *bb,
+                            CgState *st);
+__global__ void k_unscale(double *__restrict__ x, int64_t n, const CgState *st);
 __global__ void k_cg_widen(double *__restrict__ y, const float *__restrict__ x, int64_t n, const CgState *st);
 
 }  // namespace feod

@@ -55,6 +55,7 @@ def test_config2_sampled_parity():
     r = op.residual(ud).cpu().numpy()
     op.linearize(ud)
     y64 = op.jacobian_action(vd, precision=64).cpu().numpy()
+    y48 = op.jacobian_action(vd, precision=48).cpu().numpy()
     v32 = vd.float()
     y32 = op.jacobian_action(v32, precision=32).double().cpu().numpy()
     P = O.Problem(3, w.n, w.order, V, p=w.p)
@@ -69,6 +70,8 @@ def test_config2_sampled_parity():
     rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
     assert rel(r[dofs], R_ref) <= 1e-12
     assert rel(y64[dofs], Y_ref) <= 1e-12
+    assert rel(y48[dofs], Y_ref) <= 1e-12          # double-float operator, FP64 tolerance
+    assert rel(y48, y64) <= 1e-12
     _, Y32_ref = _sampled(P, u, v32.double().cpu().numpy(), dofs, w.n, w.order)
     assert rel(y32[dofs], Y32_ref) <= 1e-5
     # essential rows of J v return v, of R return 0
@@ -121,7 +124,7 @@ def test_design_fullsize_against_oracle():
 _R0_CACHE = {}
 
 
-@pytest.mark.parametrize("precision", [-32, 32, 64])
+@pytest.mark.parametrize("precision", [-32, 32, 48, 64])
 def test_config2_newton_verified_by_oracle(precision):
     """The full-size Newton solve (64^3 hexes, order 3, 7,189,057 DOFs) in each precision mode:
     the oracle evaluates ||R(u_gpu)|| on the host and confirms the GPU's 1e-8 claim."""
