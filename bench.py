@@ -489,8 +489,9 @@ def run_design(args) -> dict:
 
 def run_batched(args) -> dict:
     """64 independent instances (p ~ U[2.5,4], n in [8,40], orders 1-4, seed 5): the batched FP32
-    J v in one persistent launch against the same instances' single-instance actions one after
-    another, and the lock-step batched Newton (FP32 CG, FP64 outer) against per-instance solves."""
+    J v (autotuned: persistent launch or one launch per variant) against the same instances'
+    single-instance actions one after another, the batched action under each work policy, and the
+    lock-step batched Newton (FP32 CG, FP64 outer) against per-instance solves."""
     import torch
 
     from paper_2506_00746_gb300 import Batch, Operator
@@ -528,6 +529,15 @@ def run_batched(args) -> dict:
         for op, vi, yi in zip(ops, vs, ys):
             op.jacobian_action(vi, precision=32, out=yi)
     t_s = _event_time(seq, max(5, args.steps // 4), 3)
+    # the batched action under each work policy at the tuned tile edges (0-2: persistent launch at
+    # its default grid, 3: one launch per variant)
+    tiles = [next((t for t, w in zip(B.tiles, ws) if w.order == k), 0) for k in (1, 2, 3, 4)]
+    policy_ms = {}
+    for pol in (0, 1, 2, 3):
+        Bp = Batch(inst, tune=False, tiles=tiles, policy=pol)
+        Bp.linearize(u0)
+        policy_ms[pol] = round(_event_time(lambda: Bp.jacobian_action(v, out=y), args.steps, args.warmup) * 1e3, 4)
+        Bp.close()
     clocks = clk.stop()
     out = {"suite": "batched", "workload": "64 instances, p ~ U[2.5,4], n in [8,40], orders 1-4 (seed 5), "
                                           "%d DOFs in total" % total_dofs,
@@ -540,7 +550,7 @@ def run_batched(args) -> dict:
            "batched_jv_hbm_frac": round(bytes_alg / t_b / 1e9 / peaks["hbm_gbs"], 4),
            "sequential_jv_ms": round(t_s * 1e3, 4), "sequential_jv_gdofs": round(total_dofs / t_s / 1e9, 3),
            "sequential_jv_launches_per_step": 2 * len(ws),
-           "batching_speedup_jv": round(t_s / t_b, 3), "clocks": clocks,
+           "batching_speedup_jv": round(t_s / t_b, 3), "jv_ms_by_policy": policy_ms, "clocks": clocks,
            "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"]}
     if not args.no_newton:
         u = u0.clone()

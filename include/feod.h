@@ -293,17 +293,19 @@ const char *fe_status_string(fe_status s);
 
 /* ---------------------------------------------------------------------------------------------
  * Batched instances.  Many independent 3D problems of uneven size and order 1..4 (Eq. 1-2 each,
- * on its own mesh and law) share one persistent launch of the FP32 Jacobian action: every CTA
- * strides over a work list of (instance, tile) items and applies the item's (order, tile edge)
- * variant; a batched fix-up completes the cross-tile sums.  The batch owns one context per
+ * on its own mesh and law) share the launches of the FP32 Jacobian action: either one persistent
+ * launch whose CTAs stride over a work list of (instance, tile) items and apply each item's
+ * (order, tile edge) variant, or (work policy 3) one launch per variant with one CTA per item of
+ * that variant; a batched fix-up completes the cross-tile sums.  The batch owns one context per
  * instance.  Batch vectors are the instances' vectors concatenated, instance i at element
  * offset fe_batch_info(..., i, &offset, ...) (offsets are multiples of 64; the gaps are unused
  * and ignored).
  *
  * Autotuning (fe_batch_create): per order present, the tile edge (the largest the kernels are
  * compiled for, or the next smaller) is timed on the order's largest instance, then the
- * persistent grid (CTAs per SM) and the work order (0: instance by instance, 1: interleaved) on
- * the whole batch; results are cached in the JSON file opts->tune_cache (read first, then
+ * persistent grid (CTAs per SM) and the work policy (0: instance by instance, 1: interleaved,
+ * 2: largest instance first, each in the persistent launch; 3: one launch per variant) on the
+ * whole batch; results are cached in the JSON file opts->tune_cache (read first, then
  * rewritten), keyed by the GPU name and the batch's (order, n, tile) signature.
  * --------------------------------------------------------------------------------------------- */
 typedef struct fe_batch fe_batch;
@@ -318,8 +320,9 @@ typedef struct {
     const char *tune_cache;    /* autotuner cache file (JSON) or NULL                          */
     int tune;                  /* 1: time what the cache does not hold; 0: defaults            */
     int retune;                /* 1: ignore cached entries (and rewrite them)                  */
-    int policy;                /* work order: -1 tuned (or interleaved), 0 by instance,
-                                  1 interleaved                                                */
+    int policy;                /* work policy: -1 tuned (or interleaved), 0 by instance,
+                                  1 interleaved, 2 largest first (persistent launch), 3 one
+                                  launch per variant                                          */
     int tile[4];               /* per order 1..4: 0 tuned (or the largest), else this edge     */
 } fe_batch_opts;
 
@@ -330,13 +333,13 @@ fe_status fe_batch_create(const fe_batch_item *items, int count, const fe_batch_
                           fe_batch **out);
 /* Instance i's offset in the batch vectors, its DOF count and its tile edge (any may be NULL). */
 fe_status fe_batch_info(const fe_batch *b, int i, int64_t *offset, int64_t *n_dofs, int *tile);
-/* Batch vector length, persistent grid, threads per CTA, work order, kernels launched so far. */
+/* Batch vector length, persistent grid, threads per CTA, work policy, kernels launched so far. */
 fe_status fe_batch_shape(const fe_batch *b, int64_t *total, int *grid, int *threads, int *policy,
                          int64_t *launches);
 /* FP32 tangent of every instance at u (device double batch vector), Eq. 2. */
 fe_status fe_batch_linearize(fe_batch *b, const double *u, void *stream);
-/* y = J v for all instances in one persistent launch plus one fix-up launch; v, y: device float
- * batch vectors (not aliased).  FE_ERR_STATE before fe_batch_linearize. */
+/* y = J v for all instances in one persistent launch (policy 3: one launch per variant present)
+ * plus one fix-up launch; v, y: device float batch vectors (not aliased).  FE_ERR_STATE before fe_batch_linearize. */
 fe_status fe_batch_jacobian_action(fe_batch *b, const float *v, float *y, void *stream);
 /* Newton on every instance in lock step from u (device double batch vector, overwritten): per
  * step the FP64 residuals and FP32 tangents per instance, one Jacobi-preconditioned FP32 CG for

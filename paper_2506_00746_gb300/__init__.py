@@ -203,8 +203,9 @@ class Batch:
     ``instances``: list of dicts with keys ``vertices`` (host [(n+1)^3, 3]), ``n``, ``order`` and
     optionally ``p`` (3.0), ``eps`` (0.0), ``f_kind`` (0), ``f_const`` (1.0).  Batch vectors are
     the instances' vectors concatenated at ``offsets`` (see ``split``/``concat``).  ``tune``:
-    autotune tile edges and launch shape (cached in ``tune_cache``); ``tiles``: per order 1..4 a
-    fixed tile edge (0 = tuned).
+    autotune tile edges and launch shape (cached in ``tune_cache``); ``policy``: work policy (-1
+    tuned; 0 by instance, 1 interleaved, 2 largest first, each in one persistent launch; 3 one
+    launch per tile variant); ``tiles``: per order 1..4 a fixed tile edge (0 = tuned).
     """
 
     def __init__(self, instances, tune: bool = True, tune_cache: str | None = None, retune: bool = False,

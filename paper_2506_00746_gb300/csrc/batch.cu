@@ -206,6 +206,50 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4)
     }
 }
 
+// Work policy 3: one launch per tile variant.  CTA b runs item b of the variant's part of the work
+// list with the variant's own thread count, shared memory and register allocation -- the shape of
+// the single-instance tile kernel -- for the tiles of every instance of that variant.
+template <int D1, int TT>
+__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
+    k_jv_batch_variant(const BatchInst *__restrict__ inst, const int2 *__restrict__ items,
+                       const float *__restrict__ vb, float *__restrict__ yb, int *err)
+{
+    const int2 it = items[blockIdx.x];
+    const BatchInst &I = inst[it.x];
+    if (I.op.skip && *I.op.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+    // thread 0 initialises the barrier before it issues the copy; the other threads poll it only
+    // after the body's first barrier
+    if (!tile2_body<D1, TT, float>(I.op, c_bpairs[D1 - 2], I.T32, vb + I.off, yb + I.off, I.halo, it.y, smem + 64,
+                                   mbar, 0u, tid, CtaBar{}) &&
+        tid == 0) {
+        // the tangent block did not land within the bound: report, let the copy finish
+        atomicExch(err, 3);
+        mbar_wait_bounded(mbar, 0);
+    }
+}
+
+// the kernel of variant v (policy 3)
+const void *bv_kernel(int v)
+{
+    switch (v) {
+    case 0: return reinterpret_cast<const void *>(k_jv_batch_variant<2, 4>);
+    case 1: return reinterpret_cast<const void *>(k_jv_batch_variant<2, 2>);
+    case 2: return reinterpret_cast<const void *>(k_jv_batch_variant<3, 2>);
+    case 3: return reinterpret_cast<const void *>(k_jv_batch_variant<3, 1>);
+    case 4: return reinterpret_cast<const void *>(k_jv_batch_variant<4, 2>);
+    case 5: return reinterpret_cast<const void *>(k_jv_batch_variant<4, 1>);
+    case 6: return reinterpret_cast<const void *>(k_jv_batch_variant<5, 2>);
+    default: return reinterpret_cast<const void *>(k_jv_batch_variant<5, 1>);
+    }
+}
+
 // Batched fix-up: row r of the concatenated fix-up rows belongs to the instance i with
 // row0[i] <= r < row0[i+1] (binary search over the instances).
 struct BatchFix {
@@ -490,6 +534,7 @@ struct fe_batch {
     // launch shape (autotuned)
     int grid = 0, threads = 0, policy = 0;
     size_t smem = 0;
+    size_t vsmem[NBV] = {};               // policy 3: dynamic shared memory of each variant's launch
     int ntotal_items = 0;
     int vbeg[NBV + 1] = {};
     // device data
@@ -624,6 +669,7 @@ void free_batch_device(fe_batch *b)
 // the work list: every tile of every instance, grouped by variant; within a variant, by policy
 //   0: instance by instance;  1: interleaved (each instance's tiles spread evenly over the list);
 //   2: instances by decreasing DOF count (the largest first, the small ones fill the tail)
+//   3: as 0, run as one launch per variant (k_jv_batch_variant) instead of the persistent kernel
 // and the first variant of every CTA, in proportion to the variants' estimated work
 fe_status upload_work(fe_batch *b, int policy)
 {
@@ -703,10 +749,22 @@ fe_status launch_jv(fe_batch *b, const float *vb, float *yb, bool with_skip, cud
     W.items = b->d_items;
     for (int v = 0; v <= NBV; ++v) W.vbeg[v] = b->vbeg[v];
     W.start = b->d_start;
-    k_jv_batch<<<b->grid, BATCH_THREADS, b->smem, st>>>(inst, W, vb, yb, b->d_err, b->d_counter);
+    if (b->policy == 3) {
+        for (int v = 0; v < NBV; ++v) {
+            const int nv = b->vbeg[v + 1] - b->vbeg[v];
+            if (nv == 0) continue;
+            const int2 *items = b->d_items + b->vbeg[v];
+            void *args[] = { (void *)&inst, (void *)&items, (void *)&vb, (void *)&yb, (void *)&b->d_err };
+            BCK(cudaLaunchKernel(bv_kernel(v), dim3((unsigned)nv), dim3((unsigned)bv_threads(v)), args, b->vsmem[v], st));
+            b->launches += 1;
+        }
+    } else {
+        k_jv_batch<<<b->grid, BATCH_THREADS, b->smem, st>>>(inst, W, vb, yb, b->d_err, b->d_counter);
+        b->launches += 1;
+    }
     const unsigned fb = (unsigned)std::max<int64_t>(1, (b->nrows + 256 * FIX_ROWS - 1) / (256 * FIX_ROWS));
     k_fixup_batch<<<fb, 256, 0, st>>>(fix, b->d_row0, b->count, yb, b->d_counter);
-    b->launches += 2;
+    b->launches += 1;
     BCK(cudaGetLastError());
     return FE_OK;
 }
@@ -845,6 +903,23 @@ fe_status build_tables(fe_batch *b)
             BCK(cudaFuncSetAttribute(k_jv_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
             raised = b->smem;
         }
+    }
+    // policy 3: each variant's launch takes one tile's region (plus the mbarrier); raise each
+    // variant kernel's limit the same way
+    {
+        static std::mutex mu;
+        static size_t raised[NBV] = {};
+        std::lock_guard<std::mutex> lock(mu);
+        for (int v = 0; v < NBV; ++v) b->vsmem[v] = 0;
+        for (int i = 0; i < n; ++i) {
+            const int v = b->variant[i];
+            b->vsmem[v] = std::max(b->vsmem[v], 64 + bv_tile_bytes(v, b->ctx[i]->tqs32));
+        }
+        for (int v = 0; v < NBV; ++v)
+            if (b->vsmem[v] > raised[v] && b->vsmem[v] > 48 * 1024) {
+                BCK(cudaFuncSetAttribute(bv_kernel(v), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->vsmem[v]));
+                raised[v] = b->vsmem[v];
+            }
     }
     int per_sm = 0;
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jv_batch, b->threads, b->smem));
@@ -996,9 +1071,10 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
         } else {
             double best = 1e300;
             int bg = b->grid, bp = b->policy;
-            std::vector<int> pols = o.policy >= 0 ? std::vector<int>{ o.policy } : std::vector<int>{ 0, 1, 2 };
+            std::vector<int> pols = o.policy >= 0 ? std::vector<int>{ o.policy } : std::vector<int>{ 0, 1, 2, 3 };
             for (int pol : pols) {
-                for (int m = 1; m <= per_sm_max && s == FE_OK; ++m) {
+                // policy 3 launches one CTA per tile: the persistent grid does not apply
+                for (int m = pol == 3 ? per_sm_max : 1; m <= per_sm_max && s == FE_OK; ++m) {
                     b->grid = m * b->num_sms;
                     s = upload_work(b, pol);             // the CTAs' first variants depend on the grid
                     if (s != FE_OK) break;

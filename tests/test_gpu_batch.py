@@ -35,12 +35,14 @@ def _states(inst):
 BATCH_TILES = {1: (4, 2), 2: (2, 1), 3: (2, 1), 4: (2, 1)}
 
 
+@pytest.mark.parametrize("policy", [1, 3])
 @pytest.mark.parametrize("tiles", [[4, 2, 2, 2], [2, 1, 1, 1]])
-def test_batch_jv_matches_oracle(tiles):
+def test_batch_jv_matches_oracle(tiles, policy):
     import torch
     from paper_2506_00746_gb300 import Batch
     inst = _instances()
-    B = Batch(inst, tune=False, tiles=tiles)
+    B = Batch(inst, tune=False, tiles=tiles, policy=policy)
+    assert B.shape()["policy"] == policy
     assert B.tiles == [tiles[d["order"] - 1] for d in inst]
     us = _states(inst)
     B.linearize(B.concat(us))
@@ -79,6 +81,27 @@ def test_batch_jv_bitwise_equals_single_instance():
     B.close()
 
 
+def test_batch_policies_bitwise_equal():
+    """The persistent launch (policies 0-2) and one launch per variant (policy 3) run the same tile
+    code on the same tiles: identical results bit for bit, and the per-variant launches are
+    counted."""
+    import torch
+    from paper_2506_00746_gb300 import Batch
+    inst = _instances()
+    us = _states(inst)
+    ys = []
+    for policy in (0, 2, 3):
+        B = Batch(inst, tune=False, tiles=[4, 2, 2, 2], policy=policy)
+        B.linearize(B.concat(us))
+        v32 = B.concat([I.uniform_vector(n, seed=300 + i) for i, n in enumerate(B.n_dofs)], torch.float32)
+        l0 = B.shape()["launches"]
+        ys.append(B.jacobian_action(v32))
+        nvar = len({(d["order"], t) for d, t in zip(inst, B.tiles)})
+        assert B.shape()["launches"] - l0 == (nvar + 1 if policy == 3 else 2)
+        B.close()
+    assert torch.equal(ys[0], ys[1]) and torch.equal(ys[0], ys[2])
+
+
 def test_batch_newton_matches_oracle():
     import torch
     from paper_2506_00746_gb300 import Batch
@@ -102,6 +125,12 @@ def test_batch_newton_matches_oracle():
     assert torch.equal(a, b) and torch.equal(a, c)
     assert [r["cg_iters"] for r in ra] == [r["cg_iters"] for r in rb] == [r["cg_iters"] for r in rc]
     B.close()
+    # one launch per variant: the same iterates
+    B3 = Batch(inst, tune=False, policy=3)
+    d = B3.concat(us)
+    rd, _ = B3.newton_solve(d, use_graph=2)
+    assert torch.equal(a, d) and [r["cg_iters"] for r in rd] == [r["cg_iters"] for r in ra]
+    B3.close()
 
 
 def test_batch_autotune_cache(tmp_path):
