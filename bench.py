@@ -283,6 +283,22 @@ def run_gpu(args) -> dict | None:
         for name, _ in NEWTON_MODES[:-1]:
             if "fp64" in newton and name in newton:
                 newton[f"speedup_{name}_vs_fp64"] = round(newton["fp64"]["time_s"] / newton[name]["time_s"], 3)
+        # the same solves with Eisenstat-Walker choice 2 inner tolerances (forcing 1)
+        ew = {}
+        for name, prec in NEWTON_MODES:
+            u = u0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = op.newton_solve(u, rtol=1e-8, inner_precision=prec, max_newton=args.max_newton, forcing=1,
+                                  raise_on_error=False)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            ew[name] = {"time_s": round(max_over_ranks(wall, dev), 4), "status": rep["status"],
+                        "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
+                        "rel_residual": rep["rel"]}
+        for name, _ in NEWTON_MODES[:-1]:
+            ew[f"speedup_{name}_vs_fp64"] = round(ew["fp64"]["time_s"] / ew[name]["time_s"], 3)
+        newton["eisenstat_walker"] = ew
 
     if rank != 0:
         op.close()

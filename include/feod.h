@@ -214,7 +214,7 @@ fe_status fe_element_matrices(fe_ctx *ctx, const double *u, int method, int64_t 
 
 /* Newton-CG options.  Defaults (fe_newton_default_opts): rtol 1e-8, max_newton 50, max_cg 20000,
  * cg_rtol 1e-4, inner_precision 64, line_search 1, armijo 1e-4, max_halvings 20,
- * cg_batch 16, use_graph 2. */
+ * cg_batch 16, use_graph 2, forcing 0, eta_max 0.1. */
 typedef struct {
     double rtol;               /* stop when ||R(u_k)||_2 <= rtol ||R(u_0)||_2                    */
     int max_newton;
@@ -232,6 +232,9 @@ typedef struct {
                                   CUDA graph, host check after each; 2: the whole CG solve as
                                   one graph launch, a conditional WHILE node repeating the batch
                                   while the device-side CG flag says running                   */
+    int forcing;               /* inner CG tolerance: 0 the fixed cg_rtol; 1 Eisenstat-Walker
+                                  choice 2 (newton_solve); the batched Newton uses cg_rtol     */
+    double eta_max;            /* forcing 1: the largest inner tolerance, in (0, 1)            */
 } fe_newton_opts;
 
 #define FE_NEWTON_HIST 64
@@ -260,7 +263,11 @@ fe_status fe_newton_default_opts(fe_newton_opts *opts);
  * applied to FP64 CG vectors; dot products, norms and updates FP64.  32: the CG runs on FP32
  * vectors with the FP32 operator, for -R scaled by a power of two near its RMS (exact), with its
  * inner products accumulated in compensated FP32 (Ogita-Rump-Oishi Dot2) and summed in FP64; its
- * scalars are FP64.  All reductions run in a fixed order, so results are bitwise reproducible on
+ * scalars are FP64.  Inner tolerance: cg_rtol at every step (forcing 0), or (forcing 1) the
+ * forcing term of Eisenstat and Walker's choice 2 (SIAM J. Sci. Comput. 17, 1996): eta_0 =
+ * eta_max, eta_k = 0.9 (||R_k|| / ||R_k-1||)^2, raised to 0.9 eta_k-1^2 when that exceeds 0.1,
+ * raised to 0.5 rtol ||R_0|| / ||R_k|| (no more accuracy than the Newton stop needs), then kept
+ * in [1e-6, eta_max].  All reductions run in a fixed order, so results are bitwise reproducible on
  * a given GPU model.  Runs on an internal stream after synchronising `stream`; synchronous
  * (returns after the solve).  report may be NULL. */
 fe_status newton_solve(fe_ctx *ctx, double *u_inout, const fe_newton_opts *opts,

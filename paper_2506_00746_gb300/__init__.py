@@ -136,15 +136,18 @@ class Operator:
     # -- solvers ----------------------------------------------------------------------------
     def newton_solve(self, u, rtol: float = 1e-8, inner_precision: int = 64, cg_rtol: float = 1e-4,
                      max_newton: int = 50, max_cg: int = 20000, line_search: bool = True,
-                     cg_batch: int = 16, use_graph: int = 2, raise_on_error: bool = True, stream=None):
+                     cg_batch: int = 16, use_graph: int = 2, forcing: int = 0, eta_max: float = 0.1,
+                     raise_on_error: bool = True, stream=None):
         """Solve R(u) = 0 in place from u (Newton-CG, Jacobi-preconditioned, backtracking line search);
         returns a dict report.  inner_precision: 64 (FP64 CG), 48 (double-float J v inside an FP64
         CG), -32 (FP32 J v inside an FP64 CG) or 32 (FP32 J v and FP32 CG vectors with compensated
         inner products); the residual, norms, Newton update and line search are FP64 in every
-        mode."""
+        mode.  forcing 0: every CG to cg_rtol; 1: Eisenstat-Walker choice 2 forcing terms, at most
+        eta_max."""
         import torch
         self._chk(u, torch.float64, name="u")
         o = abi.fe_newton_default_opts()
+        o.forcing, o.eta_max = int(forcing), float(eta_max)
         o.rtol, o.inner_precision, o.cg_rtol = rtol, inner_precision, cg_rtol
         o.max_newton, o.max_cg, o.line_search = max_newton, max_cg, int(line_search)
         o.cg_batch, o.use_graph = cg_batch, int(use_graph)      # 0 plain, 1 graph batches, 2 device loop

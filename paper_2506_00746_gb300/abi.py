@@ -45,7 +45,8 @@ class fe_setup_opts(ctypes.Structure):
 class fe_newton_opts(ctypes.Structure):
     _fields_ = [("rtol", c_double), ("max_newton", c_int), ("max_cg", c_int), ("cg_rtol", c_double),
                 ("inner_precision", c_int), ("line_search", c_int), ("armijo", c_double),
-                ("max_halvings", c_int), ("cg_batch", c_int), ("use_graph", c_int)]
+                ("max_halvings", c_int), ("cg_batch", c_int), ("use_graph", c_int), ("forcing", c_int),
+                ("eta_max", c_double)]
 
 
 FE_NEWTON_HIST = 64

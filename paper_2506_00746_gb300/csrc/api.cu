@@ -931,6 +931,8 @@ extern "C" fe_status fe_newton_default_opts(fe_newton_opts *o)
     o->max_halvings = 20;
     o->cg_batch = 16;
     o->use_graph = 2;
+    o->forcing = 0;
+    o->eta_max = 0.1;
     return FE_OK;
 }
 
@@ -943,6 +945,8 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
     if (opts_in) o = *opts_in; else fe_newton_default_opts(&o);
     if (o.inner_precision != 64 && o.inner_precision != 48 && o.inner_precision != 32 && o.inner_precision != -32)
         return fail(c, FE_ERR_ARG, "inner_precision must be 64, 48, 32 or -32");
+    if (o.forcing != 0 && o.forcing != 1) return fail(c, FE_ERR_ARG, "forcing must be 0 or 1");
+    if (o.forcing == 1 && !(o.eta_max > 0.0 && o.eta_max < 1.0)) return fail(c, FE_ERR_ARG, "eta_max must lie in (0, 1)");
     fe_newton_report R;
     std::memset(&R, 0, sizeof R);
     // FP32 tangent for the FP32 operators; the FP64 one (split into FP32 word pairs before each CG
@@ -971,6 +975,7 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
     fe_status result = FE_OK;
     if (!std::isfinite(rnorm)) result = fail(c, FE_ERR_NAN, "initial residual is not finite");
     int it = 0;
+    double rprev = rnorm, eta = o.cg_rtol;
     while (result == FE_OK && rnorm > o.rtol * R.r0 && R.r0 > 0.0) {
         if (it >= o.max_newton) { result = fail(c, FE_ERR_NOT_CONVERGED, "Newton reached %d steps", it); break; }
         // Jacobi preconditioner of the current linearisation
@@ -992,9 +997,21 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
             s = prepare_tangent_df(c, st);
             if (s != FE_OK) return s;
         }
+        // inner tolerance: fixed, or the Eisenstat-Walker choice 2 forcing term
+        if (o.forcing == 1) {
+            if (it == 0) {
+                eta = o.eta_max;
+            } else {
+                const double q = rnorm / rprev, keep = 0.9 * eta * eta;
+                double e = 0.9 * q * q;
+                if (keep > 0.1) e = std::max(e, keep);
+                e = std::max(e, 0.5 * o.rtol * R.r0 / rnorm);
+                eta = std::min(std::max(e, 1e-6), o.eta_max);
+            }
+        }
         const auto c0 = std::chrono::steady_clock::now();
         int cg_it = 0, done = 0;
-        s = run_cg(c, c->w_d, o.cg_rtol, o.max_cg, jprec, o.cg_batch, o.use_graph, &cg_it, &done);
+        s = run_cg(c, c->w_d, eta, o.max_cg, jprec, o.cg_batch, o.use_graph, &cg_it, &done);
         if (s != FE_OK) return s;
         cg_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c0).count();
         R.cg_iters_total += cg_it;
@@ -1024,6 +1041,7 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
         if (!accepted) { result = fail(c, FE_ERR_BREAKDOWN, "line search failed at Newton step %d", it); break; }
         CK(cudaMemcpyAsync(u, c->w_trial, (size_t)c->nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
         std::swap(c->w_r, c->w_d);
+        rprev = rnorm;
         rnorm = tn;
         if (it < FE_NEWTON_HIST) R.r_hist[it] = rnorm;
         ++it;

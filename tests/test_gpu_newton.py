@@ -172,3 +172,29 @@ def test_device_wait_timeout_is_reported_and_context_survives():
     u = ud.clone()
     assert op.newton_solve(u, rtol=1e-8)["status"] == "FE_OK"
     op.close()
+
+
+@pytest.mark.parametrize("precision", [64, 48, -32, 32])
+def test_newton_eisenstat_walker_forcing(precision):
+    """forcing 1 (Eisenstat-Walker choice 2): the same 1e-8 solution, confirmed by the oracle's
+    residual, with fewer CG iterations in total than the fixed inner tolerance; every inner
+    tolerance stays within [1e-6, eta_max], so no CG runs to its iteration limit."""
+    import torch
+    from paper_2506_00746_gb300 import FeodError, Operator
+    V = I.lattice_vertices(3, 8, seed=0)
+    op = Operator(3, 8, 3, V, p=3.0)
+    P = O.Problem(3, 8, 3, V, p=3.0)
+    u0 = I.smooth_field(3, 8, 3, seed=1)
+    r0 = np.linalg.norm(O.residual(P, u0))
+    reps = {}
+    for forcing in (0, 1):
+        u = torch.from_numpy(u0).cuda()
+        reps[forcing] = op.newton_solve(u, rtol=1e-8, inner_precision=precision, forcing=forcing)
+        assert reps[forcing]["status"] == "FE_OK" and reps[forcing]["rel"] <= 1e-8
+        assert np.linalg.norm(O.residual(P, u.cpu().numpy())) <= 1e-8 * r0 * 1.01
+    assert reps[1]["cg_iters"] < reps[0]["cg_iters"], reps
+    with pytest.raises(FeodError):
+        op.newton_solve(torch.from_numpy(u0).cuda(), forcing=1, eta_max=1.5)
+    with pytest.raises(FeodError):
+        op.newton_solve(torch.from_numpy(u0).cuda(), forcing=2)
+    op.close()
