@@ -299,6 +299,23 @@ def run_gpu(args) -> dict | None:
         for name, _ in NEWTON_MODES[:-1]:
             ew[f"speedup_{name}_vs_fp64"] = round(ew["fp64"]["time_s"] / ew[name]["time_s"], 3)
         newton["eisenstat_walker"] = ew
+        # the small 2D configuration (16x16 quads, order 2), FP64 and mixed, beside the oracle's
+        w2 = I.WORKLOADS["2d_p3_k2_16x16"]
+        op2 = Operator(2, w2.n, w2.order, I.lattice_vertices(2, w2.n, seed=w2.mesh_seed), p=w2.p, eps=w2.eps)
+        u2 = torch.from_numpy(I.smooth_field(2, w2.n, w2.order, seed=w2.state_seed)).cuda()
+        small = {}
+        for name, prec in (("mixed", -32), ("fp64", 64)):
+            uu = u2.clone()
+            op2.newton_solve(uu, rtol=1e-8, inner_precision=prec)        # warm-up (graph creation)
+            uu = u2.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = op2.newton_solve(uu, rtol=1e-8, inner_precision=prec, raise_on_error=False)
+            torch.cuda.synchronize()
+            small[name] = {"time_s": round(time.perf_counter() - t0, 5), "status": rep["status"],
+                           "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"]}
+        op2.close()
+        newton["2d_16x16_order2"] = small
 
     if rank != 0:
         op.close()
@@ -704,9 +721,29 @@ def cpu_baseline(workload: str, budget_s: float = 12.0) -> dict:
     O.jv_partial(P, u, v, 0, m, y)
     dt = time.perf_counter() - t0
     value = P.n_dofs * (m / P.n_elems) / dt / 1e9
+    # the residual on a sample timed the same way (half the budget)
+    r = np.zeros(P.n_dofs)
+    mr = max(1, P.n_elems // 512)
+    t0 = time.perf_counter()
+    O.residual_partial(P, u, 0, mr, r)
+    dtr = time.perf_counter() - t0
+    mr = int(min(P.n_elems, max(mr, mr * 0.5 * budget_s / max(dtr, 1e-6))))
+    t0 = time.perf_counter()
+    O.residual_partial(P, u, 0, mr, r)
+    dtr = time.perf_counter() - t0
+    # the small 2D configuration's Newton solve (sparse direct inner solves), whole
+    w2 = I.WORKLOADS["2d_p3_k2_16x16"]
+    P2 = O.Problem(w2.dim, w2.n, w2.order, I.lattice_vertices(w2.dim, w2.n, seed=w2.mesh_seed), p=w2.p, eps=w2.eps)
+    u2 = I.smooth_field(w2.dim, w2.n, w2.order, seed=w2.state_seed)
+    t0 = time.perf_counter()
+    O.newton(P2, u2, rtol=1e-8)
+    dtn = time.perf_counter() - t0
     return {"value": round(value, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
             "sample": f"element-by-element FP64 J(u) v over the first {m} of {P.n_elems} elements "
-                      f"({dt:.1f} s), scaled by the element fraction"}
+                      f"({dt:.1f} s), scaled by the element fraction",
+            "residual_gdofs": round(P.n_dofs * (mr / P.n_elems) / dtr / 1e9, 6),
+            "residual_sample": f"FP64 R(u) over the first {mr} elements ({dtr:.1f} s), scaled likewise",
+            "newton_2d_16x16_s": round(dtn, 4)}
 
 
 def run_reference(args) -> dict | None:
