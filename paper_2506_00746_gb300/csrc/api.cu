@@ -319,7 +319,9 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
         const int64_t l0 = c->launches;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        c->capturing = true;
         enqueue_cg(c, batch, precision, st);
+        c->capturing = false;
         cudaError_t e = cudaStreamEndCapture(st, &g);
         c->prof = prof;
         if (e != cudaSuccess) return fail(c, FE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -353,7 +355,9 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
                 const int64_t l0 = c->launches;
                 e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
+                    c->capturing = true;
                     enqueue_cg(c, batch, precision, st);
+                    c->capturing = false;
                     k_cg_continue<<<1, 1, 0, st>>>(hc, s);
                     e = cudaStreamEndCapture(st, &body);
                 }

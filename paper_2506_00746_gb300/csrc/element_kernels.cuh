@@ -320,14 +320,26 @@ __device__ __forceinline__ void scatter_tile(const OpParams &P, int64_t t, const
     }
 }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic-serialisation
+// attribute may be scheduled while the grid before it in the stream still runs, once every CTA
+// of that grid has executed allow_dependent_launch() or exited; its grid_dependency_wait() then
+// blocks until that grid has completed and its writes are visible.  In a kernel launched without
+// the attribute the wait returns at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Fix-up: y[g] = y[g] + sum of the halo partial sums of g, in ascending tile order, accumulated
 // in the compute type TC.  Each thread takes FIX_ROWS rows (the rows of one load round are
 // consecutive across a warp) and issues the loads of all its rows before it uses them: the
 // kernel is bound by the latency of its dependent loads (row index -> value, halo entries).
+// Every CTA allows the dependent launch at once, so that a programmatically launched tile kernel
+// after it (the next Jacobian action) is scheduled into the SMs its last CTAs free; that kernel
+// waits for this grid before it reads or writes anything this one touches.
 constexpr int FIX_ROWS = 4;
 template <typename TC, typename TIO>
 __global__ void k_fixup(const FixParams F, const TC *__restrict__ halo, TIO *__restrict__ y)
 {
+    allow_dependent_launch();
     if (F.skip && *F.skip) return;
     const int64_t r0 = (int64_t)blockIdx.x * FIX_ROWS * blockDim.x + threadIdx.x;
     uint32_t g[FIX_ROWS], j0[FIX_ROWS], j1[FIX_ROWS];
@@ -1025,9 +1037,21 @@ struct Ops {
                     LaunchScope ls(c, name, st);
                     if constexpr (sizeof(TC) == 4) {
                         const size_t tsm = tile2_smem_bytes<D1, TT, TIO>(c->tqs32);
-                        k_jv_tile2<D1, TT, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(
-                            c->op, c->p32, reinterpret_cast<const float *>(Tq), v, y,
-                            reinterpret_cast<float *>(c->d_halo));
+                        // programmatic launch, except in the library's own CG graphs and under
+                        // per-kernel timing (plain stream order there)
+                        cudaLaunchAttribute at[1];
+                        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                        at[0].val.programmaticStreamSerializationAllowed = 1;
+                        cudaLaunchConfig_t cfg = {};
+                        cfg.gridDim = dim3((unsigned)grid);
+                        cfg.blockDim = dim3(TileShape<D1, TT>::THREADS);
+                        cfg.dynamicSmemBytes = tsm;
+                        cfg.stream = st;
+                        cfg.attrs = at;
+                        cfg.numAttrs = (c->capturing || c->prof) ? 0 : 1;
+                        cudaLaunchKernelEx(&cfg, k_jv_tile2<D1, TT, TIO>, c->op, c->p32,
+                                           reinterpret_cast<const float *>(Tq), v, y,
+                                           reinterpret_cast<float *>(c->d_halo));
                     } else {
                         const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
                         k_jv_tile<D1, TT, TC, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(

@@ -207,6 +207,7 @@ struct fe_ctx {
 
     // profiling / counting
     bool prof = false;
+    bool capturing = false;       // inside one of the library's own CG graph captures
     int64_t launches = 0;
     struct ProfRec { int name; cudaEvent_t a, b; };
     std::vector<ProfRec> prof_recs;

@@ -606,17 +606,37 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
     return true;
 }
 
+// Hooks that every thread of a tile runs after its slot codes are requested and before its
+// tangent copy and input values; false (uniform across the tile) passes the tile over.
+// InputsReady: nothing to wait for.  AfterPriorGrid (the single-instance kernel): wait for the
+// grid before this one in the stream (programmatic launch), then pass the tile over if the CG
+// flag says that the solve has ended.
+struct InputsReady {
+    __device__ __forceinline__ bool operator()() const { return true; }
+};
+struct AfterPriorGrid {
+    const int *skip;
+    __device__ __forceinline__ bool operator()() const
+    {
+        grid_dependency_wait();
+        return !(skip && *skip);
+    }
+};
+
 // One tile of the FP32 packed variant on a group of threads (tid: the thread's index in the group,
 // bar: the group's barrier) of at least TileShape<D1, TT>::THREADS threads (the extra threads
 // take part only in barriers).  smem: the tile's shared region (after the
 // mbarrier); mbar: an initialised mbarrier whose phase `parity` this tile's tangent copy
 // completes.  Returns false (uniformly) when the tangent copy did not land within the bound;
-// the caller then reports and waits for it again.
-template <int D1, int TT, typename TIO, typename Bar>
+// the caller then reports and waits for it again.  The slot codes (set-up data) are requested
+// first: the input values depend on them, and they are the longest chain of a tile's prologue;
+// the tangent copy (waited for only before the x stage) is issued after them.
+template <int D1, int TT, typename TIO, typename Bar, typename Ready = InputsReady>
 __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &Pr, const float *__restrict__ Tq,
                                            const TIO *__restrict__ v, TIO *__restrict__ y,
                                            float *__restrict__ halo, int64_t t, unsigned char *smem,
-                                           uint64_t *mbar, uint32_t parity, int tid, const Bar &bar)
+                                           uint64_t *mbar, uint32_t parity, int tid, const Bar &bar,
+                                           Ready inputs_ready = Ready{})
 {
     using TS = TileShape2<D1, TT>;
     constexpr int NS3 = TS::NS3, NTH = TS::THREADS;
@@ -637,10 +657,6 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
     float2 *SY2 = reinterpret_cast<float2 *>(q);        q += pad16((size_t)TS::NSY * 8);
     float *SZ1 = reinterpret_cast<float *>(q);
 
-    if (tid == 0) {
-        mbar_arrive_expect_tx(mbar, tq_bytes);
-        tma_load_1d(Tb, Tq + t * tqs, tq_bytes, mbar);
-    }
     // input gather: slot codes, then (one batch) the input values and, for halo slots, their
     // halo-array positions, which reach shared memory after the z stage
     constexpr int NPER = (NS3 + NTH - 1) / NTH;
@@ -654,6 +670,11 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
         for (int i = 0; i < NPER; ++i) {
             const int s = tid + i * NTH;
             cr[i] = gth && s < NS3 ? sl[s] : SLOT_INVALID;
+        }
+        if (!inputs_ready()) return true;
+        if (tid == 0) {
+            mbar_arrive_expect_tx(mbar, tq_bytes);
+            tma_load_1d(Tb, Tq + t * tqs, tq_bytes, mbar);
         }
         TIO vr[NPER];
 #pragma unroll
@@ -682,14 +703,16 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
         [&]() { return !bar.any(!mbar_wait_bounded(mbar, parity)); });
 }
 
-// One CTA per tile (FP32 compute; TIO float or double), as k_jv_tile.
+// One CTA per tile (FP32 compute; TIO float or double), as k_jv_tile.  Launched
+// programmatically after the fix-up of the previous action (outside graph captures): the CTAs
+// of its first wave initialise their mbarrier and request their slot codes (set-up data) while
+// that fix-up ends, then wait for it before they touch anything a kernel before them wrote.
 template <int D1, int TT, typename TIO>
 __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     k_jv_tile2(const __grid_constant__ OpParams P, const __grid_constant__ BasisPairs Pr,
                const float *__restrict__ Tq, const TIO *__restrict__ v, TIO *__restrict__ y,
                float *__restrict__ halo)
 {
-    if (P.skip && *P.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     const int tid = threadIdx.x;
@@ -699,7 +722,8 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     }
     // thread 0 initialises the barrier before it issues the copy; the other threads poll it only
     // after the body's first __syncthreads
-    if (!tile2_body<D1, TT, TIO>(P, Pr, Tq, v, y, halo, blockIdx.x, smem + 64, mbar, 0u, tid, CtaBar{}) && tid == 0) {
+    if (!tile2_body<D1, TT, TIO>(P, Pr, Tq, v, y, halo, blockIdx.x, smem + 64, mbar, 0u, tid, CtaBar{},
+                                 AfterPriorGrid{P.skip}) && tid == 0) {
         // the tangent block did not land within the bound: report, let the copy finish
         atomicExch(P.err, 3);
         mbar_wait_bounded(mbar, 0);
