@@ -378,6 +378,23 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
 // z stage) lives inside the x-stage pair array C2 (first written by the y stage), and the seam
 // planes (written from the x stage's end on) live inside the tangent buffer, which the x stage
 // has finished reading by then.
+//
+// The slot codes and halo positions are read twice: by the gather (codes, into registers) and by
+// the writes of the last stage.  The writes either read them from shared memory, where the
+// prologue stored them, or -- "late codes" -- load their own slots' entries from global memory
+// at the start of the y^T stage (the gather read the same lines a few microseconds earlier, so
+// they are L2 hits, and the y^T and z^T contractions cover the latency).  Late codes free
+// 2 x NS3 words of shared memory per tile and cost those loads; a variant takes them where the
+// smaller footprint raises the CTAs per SM that shared memory allows (GB300: 228 KB per SM,
+// 1 KB reserved per CTA, at most 2048 threads and 32 CTAs per SM): orders 3-6 of the
+// single-instance kernel (9 -> 10, 4 -> 5, 2 -> 3 and 12 -> 14 CTAs per SM), not orders 1-2.
+__host__ __device__ constexpr int tile2_ctas_per_sm(size_t smem_bytes, int threads)
+{
+    const int by_smem = (int)((size_t)228 * 1024 / (smem_bytes + 1024));
+    const int by_threads = 2048 / threads;
+    return by_smem < by_threads ? (by_smem < 32 ? by_smem : 32) : (by_threads < 32 ? by_threads : 32);
+}
+
 template <int D1, int TT>
 struct TileShape2 : TileShape<D1, TT> {
     using B = TileShape<D1, TT>;
@@ -386,6 +403,11 @@ struct TileShape2 : TileShape<D1, TT> {
     static constexpr size_t SEAM_BYTES = pad16((size_t)B::NSX * 4) + pad16((size_t)B::NSX * 8) +
                                          pad16((size_t)B::NSY * 8) + pad16((size_t)B::NSZ * 4);
     static constexpr size_t TANGENT_MIN_BYTES = (size_t)6 * TT * TT * TT * D1 * D1 * D1 * 4;
+    static constexpr size_t CODES_BYTES = 2 * pad16((size_t)B::NS3 * 4);   // slot codes + halo positions
+    static constexpr size_t CORE_BYTES = 64 + pad16(TANGENT_MIN_BYTES) + pad16((size_t)NA2 * 8) +
+                                         pad16((size_t)B::NC * 4) + pad16((size_t)B::NC * 8);
+    static constexpr bool LATE_CODES = tile2_ctas_per_sm(CORE_BYTES, B::THREADS) >
+                                       tile2_ctas_per_sm(CORE_BYTES + CODES_BYTES, B::THREADS);
 };
 
 template <int D1, int TT, typename TIO>
@@ -394,7 +416,7 @@ __host__ __device__ inline size_t tile2_smem_bytes(int64_t tqs)
     using TS = TileShape2<D1, TT>;
     static_assert(TS::SEAM_BYTES <= TS::TANGENT_MIN_BYTES, "seam planes must fit in the tangent buffer");
     static_assert((size_t)TS::NS3 * 8 <= (size_t)TS::NC * 8, "the input block must fit in C2");
-    return 64 + pad16((size_t)tqs * 4) + 2 * pad16(TS::NS3 * 4) + pad16((size_t)TS::NA2 * 8) +
+    return 64 + pad16((size_t)tqs * 4) + (TS::LATE_CODES ? 0 : TS::CODES_BYTES) + pad16((size_t)TS::NA2 * 8) +
            pad16((size_t)TS::NC * 4) + pad16((size_t)TS::NC * 8);
 }
 
@@ -417,13 +439,15 @@ struct GroupBar {
     }
 };
 
-// store_hd() runs after the z stage: it stores the halo positions that the prologue loaded into
-// registers (their latency overlaps the z stage; they are read only by the writes).
+// codes, hd: the tile's slot codes and halo positions, in shared memory or (late codes) in
+// global memory.  store_hd() runs after the z stage: it stores the halo positions that the
+// prologue loaded into registers (shared-memory codes only; their latency overlaps the z stage).
 // tangent_ready() runs in every thread before the x stage (the first reader of Tb) and returns
 // false, uniformly, to abandon the tile.
 template <int D1, int TT, typename TIO, typename Bar, typename StoreHd, typename Ready>
 __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *Tb, const TIO *Vs,
-                                             const uint32_t *codes, const uint32_t *hd, float2 *A2, float *C1,
+                                             const uint32_t *__restrict__ codes, const uint32_t *__restrict__ hd,
+                                             float2 *A2, float *C1,
                                              float2 *C2, float *SX1, float2 *SX2, float2 *SY2, float *SZ1,
                                              const TIO *__restrict__ v, TIO *__restrict__ y,
                                              float *__restrict__ halo, int tid, const Bar &bar,
@@ -527,6 +551,20 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
         }
     }
     bar.sync();
+    // the z^T stage's slots: segment h of line (zx, zy); late codes are loaded here
+    const bool actz = live && L < SE * SE;
+    const int zx = L % SE, zy = L / SE;
+    uint32_t zc[D1], zh[D1];
+    if constexpr (TS::LATE_CODES) {
+        if (actz) {
+#pragma unroll
+            for (int a = 0; a < D1; ++a) {
+                const int s = ((K * h + a) * SE + zy) * SE + zx;
+                zc[a] = codes[s];
+                zh[a] = hd[s];
+            }
+        }
+    }
     // y transpose: segment h of line (sx, qz)
     if (live && L < SE * QT) {
         const int sx = L % SE, qz = L / SE;
@@ -560,17 +598,15 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
         else SY2[h * QT * SE + L] = E[K];
     }
     bar.sync();
-    // z transpose: segment h of line (sx, sy); P^T and the writes
+    // z transpose: segment h of line (zx, zy); P^T and the writes (slot a of the segment)
     float out[D1];
-    const bool actz = live && L < SE * SE;
-    const int zx = L % SE, zy = L / SE;
-    auto write_slot = [&](int sz, float val) {
-        const int s = (sz * SE + zy) * SE + zx;
-        const uint32_t code = codes[s];
+    auto write_slot = [&](int a, float val) {
+        const int s = ((K * h + a) * SE + zy) * SE + zx;
+        const uint32_t code = TS::LATE_CODES ? zc[a] : codes[s];
         if (code == SLOT_INVALID) return;
         const uint32_t g = code & SLOT_GMASK;
         if (code & SLOT_HALO) {
-            if (!(code & SLOT_ESS)) halo[hd[s]] = val;
+            if (!(code & SLOT_ESS)) halo[TS::LATE_CODES ? zh[a] : hd[s]] = val;
         } else if (code & SLOT_ESS) {
             y[g] = v[g];
         } else {
@@ -596,13 +632,13 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
 #pragma unroll
         for (int a = 0; a < D1; ++a) out[a] = o2[a].x + o2[a].y;
 #pragma unroll
-        for (int a = 1; a < K; ++a) write_slot(K * h + a, out[a]);
+        for (int a = 1; a < K; ++a) write_slot(a, out[a]);
         if (h == 0) write_slot(0, out[0]);
-        if (h == TT - 1) write_slot(SE - 1, out[K]);
+        if (h == TT - 1) write_slot(K, out[K]);
         else SZ1[h * SE * SE + L] = out[K];
     }
     bar.sync();
-    if (actz && h > 0) write_slot(K * h, SZ1[(h - 1) * SE * SE + L] + out[0]);
+    if (actz && h > 0) write_slot(0, SZ1[(h - 1) * SE * SE + L] + out[0]);
     return true;
 }
 
@@ -645,8 +681,9 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
 
     unsigned char *p = smem;
     float *Tb = reinterpret_cast<float *>(p);           p += pad16(tq_bytes);
-    uint32_t *codes = reinterpret_cast<uint32_t *>(p);  p += pad16(NS3 * 4);
-    uint32_t *hd = reinterpret_cast<uint32_t *>(p);     p += pad16(NS3 * 4);
+    uint32_t *codes = reinterpret_cast<uint32_t *>(p);  // shared-memory codes only
+    uint32_t *hd = codes + pad16(NS3 * 4) / 4;
+    if constexpr (!TS::LATE_CODES) p += TS::CODES_BYTES;
     float2 *A2 = reinterpret_cast<float2 *>(p);         p += pad16((size_t)TS::NA2 * 8);
     float *C1 = reinterpret_cast<float *>(p);           p += pad16((size_t)TS::NC * 4);
     float2 *C2 = reinterpret_cast<float2 *>(p);
@@ -657,14 +694,14 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
     float2 *SY2 = reinterpret_cast<float2 *>(q);        q += pad16((size_t)TS::NSY * 8);
     float *SZ1 = reinterpret_cast<float *>(q);
 
-    // input gather: slot codes, then (one batch) the input values and, for halo slots, their
-    // halo-array positions, which reach shared memory after the z stage
+    // input gather: slot codes, then (one batch) the input values and, with shared-memory codes,
+    // the halo-array positions of halo slots, which reach shared memory after the z stage
     constexpr int NPER = (NS3 + NTH - 1) / NTH;
     uint32_t hr[NPER];
     const bool gth = tid < NTH;
+    const uint32_t *sl = P.slot + t * P.Spad;
+    const uint32_t *hs = P.hdst + t * P.Spad;
     {
-        const uint32_t *sl = P.slot + t * P.Spad;
-        const uint32_t *hs = P.hdst + t * P.Spad;
         uint32_t cr[NPER];
 #pragma unroll
         for (int i = 0; i < NPER; ++i) {
@@ -680,24 +717,30 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
 #pragma unroll
         for (int i = 0; i < NPER; ++i) {
             vr[i] = (cr[i] & SLOT_ESS) ? TIO(0) : v[cr[i] & SLOT_GMASK];
-            hr[i] = (cr[i] & SLOT_HALO) && !(cr[i] & SLOT_ESS) ? hs[tid + i * NTH] : 0u;
+            if constexpr (!TS::LATE_CODES) hr[i] = (cr[i] & SLOT_HALO) && !(cr[i] & SLOT_ESS) ? hs[tid + i * NTH] : 0u;
         }
 #pragma unroll
         for (int i = 0; i < NPER; ++i) {
             const int s = tid + i * NTH;
-            if (gth && s < NS3) { codes[s] = cr[i]; Vs[s] = vr[i]; }
+            if (gth && s < NS3) {
+                Vs[s] = vr[i];
+                if constexpr (!TS::LATE_CODES) codes[s] = cr[i];
+            }
         }
     }
     // makes the gathered block (and, in a new CTA, the mbarrier initialisation) visible to all
     // threads; the tangent block is waited for (bounded) only before the x stage, its first reader
     bar.sync();
     return tile_stages2<D1, TT, TIO>(
-        Pr, Tb, Vs, codes, hd, A2, C1, C2, SX1, SX2, SY2, SZ1, v, y, halo, tid, bar,
+        Pr, Tb, Vs, TS::LATE_CODES ? sl : codes, TS::LATE_CODES ? hs : hd, A2, C1, C2, SX1, SX2, SY2, SZ1, v, y,
+        halo, tid, bar,
         [&]() {
+            if constexpr (!TS::LATE_CODES) {
 #pragma unroll
-            for (int i = 0; i < NPER; ++i) {
-                const int s = tid + i * NTH;
-                if (gth && s < NS3) hd[s] = hr[i];
+                for (int i = 0; i < NPER; ++i) {
+                    const int s = tid + i * NTH;
+                    if (gth && s < NS3) hd[s] = hr[i];
+                }
             }
         },
         [&]() { return !bar.any(!mbar_wait_bounded(mbar, parity)); });
