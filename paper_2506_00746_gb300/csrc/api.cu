@@ -146,6 +146,7 @@ fe_status ensure_work(fe_ctx *c)
     CK(dalloc(c, &c->w_d, n));
     CK(dalloc(c, &c->w_trial, n));
     CK(dalloc(c, &c->w_dinv, n));
+    CK(dalloc(c, &c->w_dinv64, n));
     CK(dalloc(c, &c->w_cx, n));
     CK(dalloc(c, &c->w_cr, n));
     CK(dalloc(c, &c->w_cp, n));
@@ -244,8 +245,8 @@ void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
             else if (precision == 48) c->ops->jv_pa_df(c, c->w_cp, c->w_cq, st);
             else c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
             { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
-            { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv, n, s, c->w_partial); }
-            { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cp, c->w_cr, c->w_dinv, n, s); }
+            { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv64, n, s, c->w_partial); }
+            { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cp, c->w_cr, c->w_dinv64, n, s); }
         } else {
             c->ops->jv_pa_32(c, c->w_fp, c->w_fq, st);
             { LaunchScope ls(c, "cg_alpha32", st); k_cg_alpha32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_fp, c->w_fq, n, s, c->w_partial); }
@@ -292,11 +293,11 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
             k_scale_rhs<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cq, b, c->nl, &ds->scalar, s);
         }
         LaunchScope ls(c, "cg_init", st);
-        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cq, c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->nl, s,
+        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cq, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, c->nl, s,
                                                       rtol, max_iter, c->w_partial);
     } else if (precision != 32) {
         LaunchScope ls(c, "cg_init", st);
-        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->nl, s, rtol,
+        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, c->nl, s, rtol,
                                                       max_iter, c->w_partial);
     } else {
         CgState *ds = s + 1;
@@ -685,7 +686,7 @@ extern "C" void fe_destroy(fe_ctx *c)
     if (!c) return;
     void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_fix_off, c->d_hdst, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
                      c->d_dkr, c->d_T64, c->d_T32, c->d_Tdf, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
-                     c->w_dinv, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_fx, c->w_fr, c->w_fp, c->w_fq, c->w_state, c->w_partial };
+                     c->w_dinv, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_fx, c->w_fr, c->w_fp, c->w_fq, c->w_state, c->w_partial };
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
@@ -907,7 +908,7 @@ extern "C" fe_status fe_cg_solve(fe_ctx *c, const double *b, double *x, double r
     if (precision == 48 && (s = prepare_tangent_df(c, st)) != FE_OK) return s;
     {
         LaunchScope ls(c, "reciprocal", st);
-        k_reciprocal<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_dinv, c->d_diag, c->nl);
+        k_reciprocal<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_dinv, c->w_dinv64, c->d_diag, c->nl);
     }
     CKLAUNCH();
     int it = 0, done = 0;
@@ -987,7 +988,7 @@ extern "C" fe_status newton_solve(fe_ctx *c, double *u, const fe_newton_opts *op
         CKLAUNCH();
         {
             LaunchScope ls(c, "reciprocal", st);
-            k_reciprocal<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_dinv, c->d_diag, c->nl);
+            k_reciprocal<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_dinv, c->w_dinv64, c->d_diag, c->nl);
         }
         // right-hand side -R
         {

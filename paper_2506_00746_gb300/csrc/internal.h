@@ -181,6 +181,7 @@ struct fe_ctx {
     // Newton / CG work space (allocated on first use)
     double *w_r = nullptr, *w_d = nullptr, *w_trial = nullptr;
     float *w_dinv = nullptr;      // Jacobi scaling 1/diag(J), FP32
+    double *w_dinv64 = nullptr;   // the same values in FP64 (the FP64 CG kernels' operand)
     double *w_cx = nullptr, *w_cr = nullptr, *w_cp = nullptr, *w_cq = nullptr;   // FP64 CG
     float *w_fx = nullptr, *w_fr = nullptr, *w_fp = nullptr, *w_fq = nullptr;    // FP32 CG
     void *w_state = nullptr;      // device CG state

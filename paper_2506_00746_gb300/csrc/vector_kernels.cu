@@ -171,17 +171,29 @@ __global__ void k_design_factors(const GeomParams G, const double *__restrict__ 
 // ------------------------------------------------------------------------------------------------
 // Deterministic reductions
 // ------------------------------------------------------------------------------------------------
-// Block sum of `v` over RED_THREADS threads in a fixed tree; result valid in thread 0.
+// Block sum of `v` over RED_THREADS threads in a fixed tree (step s adds element i + s to element
+// i for i < s, s = RED_THREADS/2 ... 1); result valid in thread 0.  The steps s >= 32 run in shared
+// memory, the last five in warp 0 with shuffles: lane i adds lane i + s, the same pairs.
 __device__ __forceinline__ double block_sum(double v, double *sh)
 {
     sh[threadIdx.x] = v;
     __syncthreads();
-    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    for (int s = RED_THREADS / 2; s >= 32; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
         __syncthreads();
     }
-    return sh[0];
+    double w = 0.0;
+    if (threadIdx.x < 32) {
+        w = sh[threadIdx.x];
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) w += __shfl_down_sync(0xffffffffu, w, s);
+    }
+    return w;
 }
+
+// Grid-stride loops over [0, n) that load BATCH elements of the thread (i, i + stride, ...)
+// before they use any of them; the elements are processed in the plain loop's order.
+constexpr int BATCH = 4;
 
 // The last block to finish (ticket counter) sums the per-block partials in a fixed order.
 // Returns true in every thread of that block; *out receives the NSUM sums in thread 0.
@@ -226,14 +238,14 @@ __global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b
 }
 
 // CG start (x = 0): r = b, p = z = dinv b; rz = r.z, rr = r.r; tol2 = rtol^2 rr.
-__global__ void k_cg_init(const double *__restrict__ b, const float *__restrict__ dinv, double *__restrict__ x,
+__global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, double *__restrict__ x,
                           double *__restrict__ r, double *__restrict__ p, int64_t n, CgState *st, double rtol,
                           int max_iter, double *partial)
 {
     __shared__ double sh[RED_THREADS];
     double s[2] = { 0.0, 0.0 };
     for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
-        const double bi = b[i], zi = (double)dinv[i] * bi;
+        const double bi = b[i], zi = dinv[i] * bi;
         x[i] = 0.0; r[i] = bi; p[i] = zi;
         s[0] += bi * zi; s[1] += bi * bi;
     }
@@ -254,8 +266,19 @@ __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restric
     if (st->done) return;
     __shared__ double sh[RED_THREADS];
     double s[1] = { 0.0 };
-    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS)
-        s[0] += p[i] * q[i];
+    const int64_t gs = (int64_t)gridDim.x * RED_THREADS;
+    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += BATCH * gs) {
+        double pv[BATCH], qv[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int64_t j = i + u * gs;
+            pv[u] = j < n ? p[j] : 0.0;
+            qv[u] = j < n ? q[j] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u)
+            if (i + u * gs < n) s[0] += pv[u] * qv[u];
+    }
     double o[1];
     if (last_block_sum<1>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
         st->pq = o[0];
@@ -266,18 +289,31 @@ __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restric
 
 // x += alpha p; r -= alpha q; z = dinv r; rz' = r.z, rr = r.r; beta = rz'/rz; convergence test.
 __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ q, const float *__restrict__ dinv, int64_t n, CgState *st,
+                            const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, CgState *st,
                             double *partial)
 {
     if (st->done) return;
     __shared__ double sh[RED_THREADS];
     const double alpha = st->alpha;
     double s[2] = { 0.0, 0.0 };
-    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
-        x[i] += alpha * p[i];
-        const double ri = r[i] - alpha * q[i];
-        r[i] = ri;
-        s[0] += ri * (double)dinv[i] * ri; s[1] += ri * ri;
+    const int64_t gs = (int64_t)gridDim.x * RED_THREADS;
+    for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += BATCH * gs) {
+        double xv[BATCH], pv[BATCH], rv[BATCH], qv[BATCH], dv[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int64_t j = i + u * gs;
+            if (j < n) { xv[u] = x[j]; pv[u] = p[j]; rv[u] = r[j]; qv[u] = q[j]; dv[u] = dinv[j]; }
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int64_t j = i + u * gs;
+            if (j < n) {
+                x[j] = xv[u] + alpha * pv[u];
+                const double ri = rv[u] - alpha * qv[u];
+                r[j] = ri;
+                s[0] += ri * dv[u] * ri; s[1] += ri * ri;
+            }
+        }
     }
     double o[2];
     if (last_block_sum<2>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
@@ -291,13 +327,25 @@ __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, cons
 }
 
 // p = dinv r + beta p (skipped once converged).
-__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const float *__restrict__ dinv,
+__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
                                int64_t n, const CgState *st)
 {
     if (st->done) return;
     const double beta = st->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = (double)dinv[i] * r[i] + beta * p[i];
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += BATCH * gs) {
+        double rv[BATCH], pv[BATCH], dv[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int64_t j = i + u * gs;
+            if (j < n) { dv[u] = dinv[j]; rv[u] = r[j]; pv[u] = p[j]; }
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int64_t j = i + u * gs;
+            if (j < n) p[j] = dv[u] * rv[u] + beta * pv[u];
+        }
+    }
 }
 
 // y = a + alpha b
@@ -323,12 +371,15 @@ __global__ void k_split_df(const double *__restrict__ x, dfloat *__restrict__ y,
         y[i] = dfloat(x[i]);
 }
 
-// y = 1 / x rounded to FP32 (Jacobi preconditioner from the assembled diagonal)
-__global__ void k_reciprocal(float *__restrict__ y, const double *__restrict__ x, int64_t n)
+// y = 1 / x rounded to FP32 (Jacobi preconditioner from the assembled diagonal), and y64 the same
+// values in FP64 for the FP64 CG kernels (no conversion per use)
+__global__ void k_reciprocal(float *__restrict__ y, double *__restrict__ y64, const double *__restrict__ x, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double d = x[i];
-        y[i] = (float)(d != 0.0 ? 1.0 / d : 1.0);
+        const float r = (float)(d != 0.0 ? 1.0 / d : 1.0);
+        y[i] = r;
+        y64[i] = (double)r;
     }
 }
 

@@ -30,20 +30,20 @@ __global__ void k_design_factors(const GeomParams G, const double *__restrict__ 
                                  double kappa_q, double *__restrict__ kr, double *__restrict__ dkr);
 __global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *partial,
                       unsigned *counter, double *out);
-__global__ void k_cg_init(const double *__restrict__ b, const float *__restrict__ dinv, double *__restrict__ x,
+__global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, double *__restrict__ x,
                           double *__restrict__ r, double *__restrict__ p, int64_t n, CgState *st, double rtol,
                           int max_iter, double *partial);
 __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restrict__ q, int64_t n, CgState *st,
                            double *partial);
 __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ q, const float *__restrict__ dinv, int64_t n, CgState *st,
+                            const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, CgState *st,
                             double *partial);
-__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const float *__restrict__ dinv,
+__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
                                int64_t n, const CgState *st);
 __global__ void k_waxpy(double *__restrict__ y, const double *__restrict__ a, double alpha,
                         const double *__restrict__ b, int64_t n);
 __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, double alpha, int64_t n);
-__global__ void k_reciprocal(float *__restrict__ y, const double *__restrict__ x, int64_t n);
+__global__ void k_reciprocal(float *__restrict__ y, double *__restrict__ y64, const double *__restrict__ x, int64_t n);
 __global__ void k_split_df(const double *__restrict__ x, dfloat *__restrict__ y, int64_t n);
 __global__ void k_cg_init32(const double *__restrict__ b, const float *__restrict__ dinv, float *__restrict__ x,
                             float *__restrict__ r, float *__restrict__ p, int64_t n, CgState *st, const double *bb,
