@@ -586,6 +586,14 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
             c->bdf.B[i] = dfloat(B); c->bdf.G[i] = dfloat(G); c->bdf.B2[i] = dfloat(B * B);
             c->bdf.G2[i] = dfloat(G * G); c->bdf.BG[i] = dfloat(B * G);
         }
+    // collocation derivative: the Lagrange basis on the Gauss points, differentiated there
+    std::vector<double> cval, cder;
+    lagrange_tables(xq, xq, cval, cder);
+    for (int i = 0; i < c->q1 * c->q1; ++i) {
+        c->b64.Dc[i] = cder[i];
+        c->b32.Dc[i] = (float)cder[i];
+        c->bdf.Dc[i] = dfloat(cder[i]);
+    }
     c->gp.dim = dim; c->gp.d1 = c->d1; c->gp.q1 = c->q1; c->gp.n = n; c->gp.T = T; c->gp.nt = c->nt;
     c->gp.nepad = c->nepad; c->gp.f_kind = prob->f_kind; c->gp.f_const = prob->f_const; c->gp.p = prob->p;
 

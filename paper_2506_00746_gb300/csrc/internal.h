@@ -48,6 +48,7 @@ struct BasisT {
     T B2[MAXQ * MAXQ];   // B^2
     T G2[MAXQ * MAXQ];   // G^2
     T BG[MAXQ * MAXQ];   // B*G
+    T Dc[MAXQ * MAXQ];   // collocation derivative at the Gauss points: Dc[q][j] = l_j'(x_q)
 };
 
 // FP32 1D basis tables as pairs, for packed (two-lane) FP32 multiply-adds: BG = (B, G),

@@ -50,13 +50,17 @@ struct TileShape {
     static constexpr int NSZ = (TT - 1) * SE * SE;
 };
 
+// Shared memory of the generic (collocated) tile kernel: mbarrier, tangent block, slot codes, halo
+// positions, gathered DOF block, the z/y^T array A, the y/x^T array C, the point arrays U, FX, FY,
+// FZ and the seam planes.
 template <int D1, int TT, typename TC, typename TIO>
 __host__ __device__ inline size_t tile_smem_bytes(int64_t tqs, int /*Spad*/)
 {
     using TS = TileShape<D1, TT>;
     return 64 + pad16((size_t)tqs * sizeof(TC)) + 2 * pad16(TS::NS3 * 4) + pad16(TS::NS3 * sizeof(TIO)) +
-           pad16(2 * (size_t)TS::NA * sizeof(TC)) + pad16(3 * (size_t)TS::NC * sizeof(TC)) +
-           pad16((3 * (size_t)TS::NSX + 2 * (size_t)TS::NSY + (size_t)TS::NSZ) * sizeof(TC));
+           pad16((size_t)TS::NA * sizeof(TC)) + pad16((size_t)TS::NC * sizeof(TC)) +
+           4 * pad16((size_t)TS::NQT * sizeof(TC)) +
+           pad16(((size_t)TS::NSX + (size_t)TS::NSY + (size_t)TS::NSZ) * sizeof(TC));
 }
 
 // n consecutive shared-memory values into registers; 16-byte vector loads when n % 4 == 0 (FP32)
@@ -83,164 +87,228 @@ __device__ __forceinline__ void lds_run(const TC *p, TC (&r)[N])
     }
 }
 
-// One tile from shared memory: z, y, x (+ D + x^T), y^T, z^T stages and the writes.  Tb: the
-// tile's tangent block, Vs: its gathered DOF block (I/O type), codes: its slot codes, hd: the
-// halo-array position of each halo slot's partial sum.
-template <int D1, int TT, typename TC, typename TIO>
-__device__ __forceinline__ void tile_stages(const OpParams &P, const BasisT<TC> &Bs, int64_t t, const TC *Tb,
-                                            const TIO *Vs, const uint32_t *codes, const uint32_t *hd, TC *AE,
-                                            TC *Cb, TC *SX, TC *SY, TC *SZ, const TIO *__restrict__ v,
-                                            TIO *__restrict__ y, TC *__restrict__ halo, int tid)
-{
+// Collocated stages of the generic (FP64 and double-float) tile kernel.  The forward half
+// interpolates the tile's DOF block to its quadrature points (B along z, y, x), then takes the
+// reference gradient there with the Q1 x Q1 collocation derivative Dc (Dc[q][j] = l_j'(x_q), l_j
+// the Lagrange polynomials on the Gauss points; exact, as the interpolant has degree k = Q1 - 1
+// in each direction).  The backward half applies Dc^T along x, y, z, sums, and applies B^T along
+// x, y, z.  That is 12 D1^4 + 9 D1^3 multiply-adds per element, the algorithmic count, where
+// carrying (B, G) pairs through the stages takes 16 D1^4 + 9 D1^3.
+//
+// Every stage is a function of the thread index over shared-memory arrays, run between barriers:
+//   z  (line (sx, sy) of slots, segment h):  A = B_z v
+//   y  (line (sx, qz)):                      C = B_y A
+//   x1 (line (qy, qz)):                      U = B_x C                     (values at the points)
+//   x2 (line (qy, qz)):                      g = (Dc_x U, Dc_y U, Dc_z U), f = T g -> FX, FY, FZ
+//   x3 (line (qy, qz)):                      W = Dc_x^T FX + Dc_y^T FY + Dc_z^T FZ, C = B_x^T W
+//   yT (line (sx, qz)):                      A = B_y^T C
+//   zT (line (sx, sy)):                      out = B_z^T A, written through the slot codes
+// with seam planes for the DOFs that neighbouring segments share (left term first).  The point
+// arrays U, FX, FY, FZ are indexed (qx, qy, qz) -> qz + QT (qy + QT qx).  The functions are host-
+// callable so that a host loop over the thread indices can run them between the same barriers.
+template <int D1, int TT>
+struct Colloc {
     using TS = TileShape<D1, TT>;
-    constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT;
-    constexpr int SA = TS::SA, NA = TS::NA, NC = TS::NC, NLP = TS::NLP;
-    constexpr int NSX = TS::NSX, NSY = TS::NSY;
-    const int L = tid % NLP, h = tid / NLP;     // line (lanes walk consecutive lines), segment
+    static constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT;
+    static constexpr int SA = TS::SA, NLP = TS::NLP;
+    __host__ __device__ static constexpr int pidx(int qx, int qy, int qz) { return qz + QT * (qy + QT * qx); }
 
-    // z: segment h (element along z) of line (sx, sy): K+1 slots -> Q1 points, B^ and G^
-    if (L < SE * SE) {
+    template <typename TC, typename TIO>
+    __host__ __device__ static void z(const BasisT<TC> &Bs, const TIO *Vs, TC *A, int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= SE * SE) return;
         const int sx = L % SE, sy = L / SE;
         TC in[D1];
 #pragma unroll
         for (int a = 0; a < D1; ++a) in[a] = (TC)Vs[((K * h + a) * SE + sy) * SE + sx];
 #pragma unroll
         for (int q = 0; q < Q1; ++q) {
-            TC a0 = TC(0), a1 = TC(0);
+            TC acc = TC(0);
 #pragma unroll
-            for (int a = 0; a < D1; ++a) { a0 += Bs.B[q * D1 + a] * in[a]; a1 += Bs.G[q * D1 + a] * in[a]; }
-            const int o = sx + SE * (Q1 * h + q) + SA * sy;
-            AE[o] = a0;
-            AE[NA + o] = a1;
+            for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * in[a];
+            A[sx + SE * (Q1 * h + q) + SA * sy] = acc;
         }
     }
-    __syncthreads();
-    // y: segment h of line (sx, qz)
-    if (L < SE * QT) {
+
+    template <typename TC>
+    __host__ __device__ static void y(const BasisT<TC> &Bs, const TC *A, TC *C, int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= SE * QT) return;
         const int sx = L % SE, qz = L / SE;
-        TC a0[D1], a1[D1];
+        TC in[D1];
 #pragma unroll
-        for (int a = 0; a < D1; ++a) {
-            const int o = sx + SE * qz + SA * (K * h + a);
-            a0[a] = AE[o];
-            a1[a] = AE[NA + o];
-        }
+        for (int a = 0; a < D1; ++a) in[a] = A[sx + SE * qz + SA * (K * h + a)];
 #pragma unroll
         for (int q = 0; q < Q1; ++q) {
-            TC c00 = TC(0), c01 = TC(0), c10 = TC(0);
+            TC acc = TC(0);
 #pragma unroll
-            for (int a = 0; a < D1; ++a) {
-                c00 += Bs.B[q * D1 + a] * a0[a];
-                c01 += Bs.G[q * D1 + a] * a0[a];
-                c10 += Bs.B[q * D1 + a] * a1[a];
-            }
-            const int o = sx + SE * qz + SE * QT * (Q1 * h + q);
-            Cb[o] = c00;
-            Cb[NC + o] = c01;
-            Cb[2 * NC + o] = c10;
+            for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * in[a];
+            C[sx + SE * qz + SE * QT * (Q1 * h + q)] = acc;
         }
     }
-    __syncthreads();
-    // x: segment h (element column ex = h) of line (qy, qz): gradient, D, x transpose
-    TC d00[D1], d01[D1], d10[D1];
-    const bool actx = L < QT * QT;
-    const int xqz = L % QT, xqy = L / QT;
-    const int xo = SE * xqz + SE * QT * xqy + K * h;
-    if (actx) {
-        TC c00[D1], c01[D1], c10[D1];
+
+    template <typename TC>
+    __host__ __device__ static void x1(const BasisT<TC> &Bs, const TC *C, TC *U, int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= QT * QT) return;
+        const int qz = L % QT, qy = L / QT;
+        const int xo = SE * qz + SE * QT * qy + K * h;
+        TC in[D1];
 #pragma unroll
-        for (int a = 0; a < D1; ++a) {
-            c00[a] = Cb[xo + a]; c01[a] = Cb[NC + xo + a]; c10[a] = Cb[2 * NC + xo + a];
-            d00[a] = TC(0); d01[a] = TC(0); d10[a] = TC(0);
-        }
-        const TC *Tl = Tb + Q1 * (xqz + QT * (xqy + QT * h));
-        TC txx[Q1], tyy[Q1], tzz[Q1], txy[Q1], txz[Q1], tyz[Q1];
-        lds_run<Q1, TC>(Tl, txx);
-        lds_run<Q1, TC>(Tl + NQT, tyy);
-        lds_run<Q1, TC>(Tl + 2 * NQT, tzz);
-        lds_run<Q1, TC>(Tl + 3 * NQT, txy);
-        lds_run<Q1, TC>(Tl + 4 * NQT, txz);
-        lds_run<Q1, TC>(Tl + 5 * NQT, tyz);
+        for (int a = 0; a < D1; ++a) in[a] = C[xo + a];
 #pragma unroll
         for (int q = 0; q < Q1; ++q) {
+            TC acc = TC(0);
+#pragma unroll
+            for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * in[a];
+            U[pidx(Q1 * h + q, qy, qz)] = acc;
+        }
+    }
+
+    // Tb: the tile's tangent block, layout [6][ex][qy][qz][qx] (qx element-local), components
+    // xx yy zz xy xz yz of the symmetric dq/dg
+    template <typename TC>
+    __host__ __device__ static void x2(const BasisT<TC> &Bs, const TC *Tb, const TC *U, TC *FX, TC *FY, TC *FZ,
+                                       int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= QT * QT) return;
+        const int qz = L % QT, qy = L / QT;
+        const int y0 = Q1 * (qy / Q1), yl = qy % Q1, z0 = Q1 * (qz / Q1), zl = qz % Q1;
+        const TC *Tl = Tb + Q1 * (qz + QT * (qy + QT * h));
+        TC u[Q1];
+#pragma unroll
+        for (int j = 0; j < Q1; ++j) u[j] = U[pidx(Q1 * h + j, qy, qz)];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            const int qx = Q1 * h + q;
             TC gx = TC(0), gy = TC(0), gz = TC(0);
 #pragma unroll
-            for (int a = 0; a < D1; ++a) {
-                gx += Bs.G[q * D1 + a] * c00[a];
-                gy += Bs.B[q * D1 + a] * c01[a];
-                gz += Bs.B[q * D1 + a] * c10[a];
+            for (int j = 0; j < Q1; ++j) {
+                gx += Bs.Dc[q * Q1 + j] * u[j];
+                gy += Bs.Dc[yl * Q1 + j] * U[pidx(qx, y0 + j, qz)];
+                gz += Bs.Dc[zl * Q1 + j] * U[pidx(qx, qy, z0 + j)];
             }
-            const TC fx = txx[q] * gx + txy[q] * gy + txz[q] * gz;
-            const TC fy = txy[q] * gx + tyy[q] * gy + tyz[q] * gz;
-            const TC fz = txz[q] * gx + tyz[q] * gy + tzz[q] * gz;
-#pragma unroll
-            for (int a = 0; a < D1; ++a) {
-                d00[a] += Bs.G[q * D1 + a] * fx;
-                d01[a] += Bs.B[q * D1 + a] * fy;
-                d10[a] += Bs.B[q * D1 + a] * fz;
-            }
+            const TC txx = Tl[q], tyy = Tl[NQT + q], tzz = Tl[2 * NQT + q];
+            const TC txy = Tl[3 * NQT + q], txz = Tl[4 * NQT + q], tyz = Tl[5 * NQT + q];
+            FX[pidx(qx, qy, qz)] = txx * gx + txy * gy + txz * gz;
+            FY[pidx(qx, qy, qz)] = txy * gx + tyy * gy + tyz * gz;
+            FZ[pidx(qx, qy, qz)] = txz * gx + tyz * gy + tzz * gz;
         }
     }
-    __syncthreads();       // every segment has read its c values before any is overwritten
-    if (actx) {
+
+    template <typename TC>
+    __host__ __device__ static void x3(const BasisT<TC> &Bs, const TC *FX, const TC *FY, const TC *FZ, TC *C,
+                                       TC *SX, int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= QT * QT) return;
+        const int qz = L % QT, qy = L / QT;
+        const int y0 = Q1 * (qy / Q1), yl = qy % Q1, z0 = Q1 * (qz / Q1), zl = qz % Q1;
+        const int xo = SE * qz + SE * QT * qy + K * h;
+        TC d[D1];
 #pragma unroll
-        for (int a = 0; a < K; ++a) { Cb[xo + a] = d00[a]; Cb[NC + xo + a] = d01[a]; Cb[2 * NC + xo + a] = d10[a]; }
-        if (h == TT - 1) {
-            Cb[xo + K] = d00[K]; Cb[NC + xo + K] = d01[K]; Cb[2 * NC + xo + K] = d10[K];
-        } else {
-            const int so = h * QT * QT + L;
-            SX[so] = d00[K]; SX[NSX + so] = d01[K]; SX[2 * NSX + so] = d10[K];
+        for (int a = 0; a < D1; ++a) d[a] = TC(0);
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            const int qx = Q1 * h + q;
+            TC w = TC(0);
+#pragma unroll
+            for (int j = 0; j < Q1; ++j) {
+                w += Bs.Dc[j * Q1 + q] * FX[pidx(Q1 * h + j, qy, qz)];
+                w += Bs.Dc[j * Q1 + yl] * FY[pidx(qx, y0 + j, qz)];
+                w += Bs.Dc[j * Q1 + zl] * FZ[pidx(qx, qy, z0 + j)];
+            }
+#pragma unroll
+            for (int a = 0; a < D1; ++a) d[a] += Bs.B[q * D1 + a] * w;
         }
+#pragma unroll
+        for (int a = 0; a < K; ++a) C[xo + a] = d[a];
+        if (h == TT - 1) C[xo + K] = d[K];
+        else SX[h * QT * QT + L] = d[K];
     }
-    __syncthreads();
-    // y transpose: segment h (element along y) of line (sx, qz)
-    if (L < SE * QT) {
+
+    template <typename TC>
+    __host__ __device__ static void yT(const BasisT<TC> &Bs, const TC *C, const TC *SX, TC *A, TC *SY, int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= SE * QT) return;
         const int sx = L % SE, qz = L / SE;
         const bool xseam = (sx % K == 0) && sx > 0 && sx < SE - 1;
-        TC e00[Q1], e01[Q1], e10[Q1];
+        TC e[Q1];
 #pragma unroll
         for (int q = 0; q < Q1; ++q) {
             const int qy = Q1 * h + q;
-            const int o = sx + SE * qz + SE * QT * qy;
-            e00[q] = Cb[o]; e01[q] = Cb[NC + o]; e10[q] = Cb[2 * NC + o];
-            if (xseam) {
-                const int so = (sx / K - 1) * QT * QT + qz + QT * qy;
-                e00[q] = SX[so] + e00[q]; e01[q] = SX[NSX + so] + e01[q]; e10[q] = SX[2 * NSX + so] + e10[q];
-            }
+            e[q] = C[sx + SE * qz + SE * QT * qy];
+            if (xseam) e[q] = SX[(sx / K - 1) * QT * QT + qz + QT * qy] + e[q];
         }
-        TC E0[D1], E1[D1];
+        TC E[D1];
 #pragma unroll
-        for (int a = 0; a < D1; ++a) { E0[a] = TC(0); E1[a] = TC(0); }
+        for (int a = 0; a < D1; ++a) E[a] = TC(0);
 #pragma unroll
         for (int q = 0; q < Q1; ++q)
 #pragma unroll
-            for (int a = 0; a < D1; ++a) {
-                E0[a] += Bs.B[q * D1 + a] * e00[q] + Bs.G[q * D1 + a] * e01[q];
-                E1[a] += Bs.B[q * D1 + a] * e10[q];
-            }
+            for (int a = 0; a < D1; ++a) E[a] += Bs.B[q * D1 + a] * e[q];
 #pragma unroll
-        for (int a = 0; a < K; ++a) {
-            const int o = sx + SE * qz + SA * (K * h + a);
-            AE[o] = E0[a];
-            AE[NA + o] = E1[a];
-        }
-        if (h == TT - 1) {
-            const int o = sx + SE * qz + SA * (SE - 1);
-            AE[o] = E0[K];
-            AE[NA + o] = E1[K];
-        } else {
-            const int so = h * QT * SE + L;
-            SY[so] = E0[K];
-            SY[NSY + so] = E1[K];
-        }
+        for (int a = 0; a < K; ++a) A[sx + SE * qz + SA * (K * h + a)] = E[a];
+        if (h == TT - 1) A[sx + SE * qz + SA * (SE - 1)] = E[K];
+        else SY[h * QT * SE + L] = E[K];
     }
-    __syncthreads();
-    // z transpose: segment h (element along z) of line (sx, sy); P^T and the writes
-    TC out[D1];
-    const bool actz = L < SE * SE;
-    const int zx = L % SE, zy = L / SE;
-    auto write_slot = [&](int sz, TC val) {
-        const int s = (sz * SE + zy) * SE + zx;
+
+    // out0: this thread's term of slot K h, added by seam() after the next barrier (h > 0)
+    template <typename TC, typename W>
+    __host__ __device__ static void zT(const BasisT<TC> &Bs, const TC *A, const TC *SY, TC *SZ, const W &write,
+                                       TC &out0, int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= SE * SE) return;
+        const int zx = L % SE, zy = L / SE;
+        const bool yseam = (zy % K == 0) && zy > 0 && zy < SE - 1;
+        TC zv[Q1];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) {
+            const int qz = Q1 * h + q;
+            zv[q] = A[zx + SE * qz + SA * zy];
+            if (yseam) zv[q] = SY[(zy / K - 1) * QT * SE + zx + SE * qz] + zv[q];
+        }
+        TC out[D1];
+#pragma unroll
+        for (int a = 0; a < D1; ++a) out[a] = TC(0);
+#pragma unroll
+        for (int q = 0; q < Q1; ++q)
+#pragma unroll
+            for (int a = 0; a < D1; ++a) out[a] += Bs.B[q * D1 + a] * zv[q];
+        const int s0 = zy * SE + zx;
+#pragma unroll
+        for (int a = 1; a < K; ++a) write((K * h + a) * SE * SE + s0, out[a]);
+        if (h == 0) write(s0, out[0]);
+        if (h == TT - 1) write((SE - 1) * SE * SE + s0, out[K]);
+        else SZ[h * SE * SE + L] = out[K];
+        out0 = out[0];
+    }
+
+    template <typename TC, typename W>
+    __host__ __device__ static void seam(const TC *SZ, const W &write, TC out0, int tid)
+    {
+        const int L = tid % NLP, h = tid / NLP;
+        if (L >= SE * SE || h == 0) return;
+        write((K * h * SE + L / SE) * SE + L % SE, SZ[(h - 1) * SE * SE + L] + out0);
+    }
+};
+
+// The writes of one tile: P^T (essential rows: J v = v), the halo partial sums of slots that a
+// neighbouring tile owns, the tile's own DOFs.
+template <typename TC, typename TIO>
+struct SlotWriter {
+    const uint32_t *codes, *hd;
+    const TIO *v;
+    TIO *y;
+    TC *halo;
+    __host__ __device__ void operator()(int s, TC val) const
+    {
         const uint32_t code = codes[s];
         if (code == SLOT_INVALID) return;
         const uint32_t g = code & SLOT_GMASK;
@@ -251,39 +319,8 @@ __device__ __forceinline__ void tile_stages(const OpParams &P, const BasisT<TC> 
         } else {
             y[g] = (TIO)val;
         }
-    };
-    if (actz) {
-        const bool yseam = (zy % K == 0) && zy > 0 && zy < SE - 1;
-        TC z0[Q1], z1[Q1];
-#pragma unroll
-        for (int q = 0; q < Q1; ++q) {
-            const int qz = Q1 * h + q;
-            const int o = zx + SE * qz + SA * zy;
-            z0[q] = AE[o];
-            z1[q] = AE[NA + o];
-            if (yseam) {
-                const int so = (zy / K - 1) * QT * SE + zx + SE * qz;
-                z0[q] = SY[so] + z0[q];
-                z1[q] = SY[NSY + so] + z1[q];
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < D1; ++a) out[a] = TC(0);
-#pragma unroll
-        for (int q = 0; q < Q1; ++q)
-#pragma unroll
-            for (int a = 0; a < D1; ++a) out[a] += Bs.B[q * D1 + a] * z0[q] + Bs.G[q * D1 + a] * z1[q];
-        // slots that only this segment touches
-#pragma unroll
-        for (int a = 1; a < K; ++a) write_slot(K * h + a, out[a]);
-        if (h == 0) write_slot(0, out[0]);
-        if (h == TT - 1) write_slot(SE - 1, out[K]);
-        else SZ[h * SE * SE + L] = out[K];
     }
-    __syncthreads();
-    // z seams: left segment's term, then this segment's
-    if (actz && h > 0) write_slot(K * h, SZ[(h - 1) * SE * SE + L] + out[0]);
-}
+};
 
 // One CTA per tile.  Thread 0 starts the bulk copy of the tile's tangent block; meanwhile all
 // threads load the slot codes, then (in one batch) the input values and, for halo slots, their
@@ -299,7 +336,9 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
               const TIO *__restrict__ v, TIO *__restrict__ y, TC *__restrict__ halo)
 {
     using TS = TileShape<D1, TT>;
-    constexpr int NS3 = TS::NS3, NA = TS::NA, NC = TS::NC, NSX = TS::NSX, NSY = TS::NSY, NTH = TS::THREADS;
+    using S = Colloc<D1, TT>;
+    constexpr int NS3 = TS::NS3, NA = TS::NA, NC = TS::NC, NQT = TS::NQT, NSX = TS::NSX, NSY = TS::NSY;
+    constexpr int NTH = TS::THREADS;
     if (P.skip && *P.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t t = blockIdx.x;
@@ -313,11 +352,15 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
     uint32_t *codes = reinterpret_cast<uint32_t *>(p);  p += pad16(NS3 * 4);
     uint32_t *hd = reinterpret_cast<uint32_t *>(p);     p += pad16(NS3 * 4);
     TIO *Vs = reinterpret_cast<TIO *>(p);               p += pad16(NS3 * sizeof(TIO));
-    TC *AE = reinterpret_cast<TC *>(p);                 p += pad16(2 * (size_t)NA * sizeof(TC));
-    TC *Cb = reinterpret_cast<TC *>(p);                 p += pad16(3 * (size_t)NC * sizeof(TC));
+    TC *A = reinterpret_cast<TC *>(p);                  p += pad16((size_t)NA * sizeof(TC));
+    TC *C = reinterpret_cast<TC *>(p);                  p += pad16((size_t)NC * sizeof(TC));
+    TC *U = reinterpret_cast<TC *>(p);                  p += pad16((size_t)NQT * sizeof(TC));
+    TC *FX = reinterpret_cast<TC *>(p);                 p += pad16((size_t)NQT * sizeof(TC));
+    TC *FY = reinterpret_cast<TC *>(p);                 p += pad16((size_t)NQT * sizeof(TC));
+    TC *FZ = reinterpret_cast<TC *>(p);                 p += pad16((size_t)NQT * sizeof(TC));
     TC *SX = reinterpret_cast<TC *>(p);
-    TC *SY = SX + 3 * NSX;
-    TC *SZ = SY + 2 * NSY;
+    TC *SY = SX + NSX;
+    TC *SZ = SY + NSY;
 
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -358,7 +401,23 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
         }
         return;
     }
-    tile_stages<D1, TT, TC, TIO>(P, Bs, t, Tb, Vs, codes, hd, AE, Cb, SX, SY, SZ, v, y, halo, tid);
+    const SlotWriter<TC, TIO> write{ codes, hd, v, y, halo };
+    TC out0 = TC(0);
+    S::z(Bs, Vs, A, tid);
+    __syncthreads();
+    S::y(Bs, A, C, tid);
+    __syncthreads();
+    S::x1(Bs, C, U, tid);
+    __syncthreads();
+    S::x2(Bs, Tb, U, FX, FY, FZ, tid);
+    __syncthreads();
+    S::x3(Bs, FX, FY, FZ, C, SX, tid);
+    __syncthreads();
+    S::yT(Bs, C, SX, A, SY, tid);
+    __syncthreads();
+    S::zT(Bs, A, SY, SZ, write, out0, tid);
+    __syncthreads();
+    S::seam(SZ, write, out0, tid);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -1,0 +1,123 @@
+// Host run of the collocated tile stages (Colloc<D1, TT> of the generic FP64 / double-float tile
+// kernel) against a per-element tensor-product Jacobian action on the same tile.  Each stage is a
+// host-callable function of the thread index; a loop over the thread indices runs it between the
+// same barriers as the kernel.  Random slot values and a random symmetric tangent per point; every
+// work array sits between guard regions (an access outside reads a huge sentinel or overwrites
+// one) and starts as NaN (a read of an unwritten entry shows in the result).  Checks, per tile
+// shape: agreement with the reference to 1e-13 of its largest entry, every slot written exactly
+// once, no guard touched, every output finite.  Exit status 0 when all shapes pass.
+#include "element_kernels.cuh"
+#include <cstdio>
+#include <cmath>
+#include <random>
+namespace feod {
+void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &w);
+void gll_nodes(int k, std::vector<double> &x);
+void lagrange_tables(const std::vector<double> &nodes, const std::vector<double> &pts, std::vector<double> &val,
+                     std::vector<double> &der);
+}
+using namespace feod;
+
+template <int D1, int TT>
+double run(unsigned seed)
+{
+    using TS = TileShape<D1, TT>;
+    using S = Colloc<D1, TT>;
+    constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT, NS3 = TS::NS3;
+    BasisT<double> Bs{};
+    std::vector<double> gx, gw, nodes, val, der, cval, cder;
+    gauss_legendre(Q1, gx, gw); gll_nodes(K, nodes);
+    std::vector<double> xq(Q1), xn(D1);
+    for (int q = 0; q < Q1; ++q) xq[q] = 0.5 * (gx[q] + 1.0);
+    for (int a = 0; a < D1; ++a) xn[a] = 0.5 * (nodes[a] + 1.0);
+    lagrange_tables(xn, xq, val, der);
+    lagrange_tables(xq, xq, cval, cder);
+    for (int i = 0; i < Q1 * D1; ++i) { Bs.B[i] = val[i]; Bs.G[i] = der[i]; }
+    for (int i = 0; i < Q1 * Q1; ++i) Bs.Dc[i] = cder[i];
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U01(-1.0, 1.0);
+    std::vector<double> Vs(NS3), Tb(6 * NQT);
+    for (auto &x : Vs) x = U01(rng);
+    for (auto &x : Tb) x = U01(rng);
+    // emulated shared memory (poisoned with NaN so that an unwritten read shows)
+    const double nan = std::nan("");
+    // every array sits between guard regions of 4096 sentinels; any access outside reads a
+    // sentinel (huge, shows in the result) or overwrites one (checked below)
+    constexpr int GRD = 4096;
+    const double SENT = 1e300;
+    std::vector<std::vector<double>> store;
+    auto arr = [&](int n, double fill) {
+        store.emplace_back(std::vector<double>(n + 2 * GRD, SENT));
+        for (int i = 0; i < n; ++i) store.back()[GRD + i] = fill;
+        return store.size() - 1;
+    };
+    const size_t iA = arr(TS::NA, nan), iC = arr(TS::NC, nan), iU = arr(NQT, nan), iFX = arr(NQT, nan),
+                 iFY = arr(NQT, nan), iFZ = arr(NQT, nan), iSX = arr(TS::NSX, nan), iSY = arr(TS::NSY, nan),
+                 iSZ = arr(TS::NSZ, nan);
+    auto P_ = [&](size_t i) { return store[i].data() + GRD; };
+    double *A = P_(iA), *C = P_(iC), *Uq = P_(iU), *FX = P_(iFX), *FY = P_(iFY), *FZ = P_(iFZ);
+    double *SX = P_(iSX), *SY = P_(iSY), *SZ = P_(iSZ);
+    std::vector<uint32_t> codes(NS3), hd(NS3, 0);
+    for (int s = 0; s < NS3; ++s) codes[s] = (uint32_t)s;
+    std::vector<double> v(NS3, 0.0), y(NS3, nan), halo(1, 0.0), out0(TS::THREADS, 0.0);
+    std::vector<int> writes(NS3, 0);
+    struct CountingWriter {
+        SlotWriter<double, double> w; int *cnt;
+        void operator()(int s, double val) const { cnt[s]++; w(s, val); }
+    } write{ SlotWriter<double, double>{ codes.data(), hd.data(), v.data(), y.data(), halo.data() }, writes.data() };
+    const int NT = TS::THREADS;
+    for (int t = 0; t < NT; ++t) S::z(Bs, Vs.data(), A, t);
+    for (int t = 0; t < NT; ++t) S::y(Bs, A, C, t);
+    for (int t = 0; t < NT; ++t) S::x1(Bs, C, Uq, t);
+    for (int t = 0; t < NT; ++t) S::x2(Bs, Tb.data(), Uq, FX, FY, FZ, t);
+    for (int t = 0; t < NT; ++t) S::x3(Bs, FX, FY, FZ, C, SX, t);
+    for (int t = 0; t < NT; ++t) S::yT(Bs, C, SX, A, SY, t);
+    for (int t = 0; t < NT; ++t) S::zT(Bs, A, SY, SZ, write, out0[t], t);
+    for (int t = 0; t < NT; ++t) S::seam(SZ, write, out0[t], t);
+    // reference: per element, full tensor products
+    std::vector<double> yr(NS3, 0.0);
+    for (int ez = 0; ez < TT; ++ez) for (int ey = 0; ey < TT; ++ey) for (int ex = 0; ex < TT; ++ex)
+    for (int qz = 0; qz < Q1; ++qz) for (int qy = 0; qy < Q1; ++qy) for (int qx = 0; qx < Q1; ++qx) {
+        double g[3] = { 0, 0, 0 };
+        for (int c = 0; c < D1; ++c) for (int b = 0; b < D1; ++b) for (int a = 0; a < D1; ++a) {
+            const int s = ((ez * K + c) * SE + ey * K + b) * SE + ex * K + a;
+            const double Bx = Bs.B[qx * D1 + a], By = Bs.B[qy * D1 + b], Bz = Bs.B[qz * D1 + c];
+            const double Gx = Bs.G[qx * D1 + a], Gy = Bs.G[qy * D1 + b], Gz = Bs.G[qz * D1 + c];
+            g[0] += Gx * By * Bz * Vs[s]; g[1] += Bx * Gy * Bz * Vs[s]; g[2] += Bx * By * Gz * Vs[s];
+        }
+        const int ti = ((ex * QT + ey * Q1 + qy) * QT + ez * Q1 + qz) * Q1 + qx;
+        const double txx = Tb[ti], tyy = Tb[NQT + ti], tzz = Tb[2 * NQT + ti];
+        const double txy = Tb[3 * NQT + ti], txz = Tb[4 * NQT + ti], tyz = Tb[5 * NQT + ti];
+        const double f[3] = { txx * g[0] + txy * g[1] + txz * g[2], txy * g[0] + tyy * g[1] + tyz * g[2],
+                              txz * g[0] + tyz * g[1] + tzz * g[2] };
+        for (int c = 0; c < D1; ++c) for (int b = 0; b < D1; ++b) for (int a = 0; a < D1; ++a) {
+            const int s = ((ez * K + c) * SE + ey * K + b) * SE + ex * K + a;
+            const double Bx = Bs.B[qx * D1 + a], By = Bs.B[qy * D1 + b], Bz = Bs.B[qz * D1 + c];
+            const double Gx = Bs.G[qx * D1 + a], Gy = Bs.G[qy * D1 + b], Gz = Bs.G[qz * D1 + c];
+            yr[s] += Gx * By * Bz * f[0] + Bx * Gy * Bz * f[1] + Bx * By * Gz * f[2];
+        }
+    }
+    double err = 0.0, nrm = 0.0;
+    int bad_writes = 0, guards = 0, nonfinite = 0;
+    for (auto &a : store) {
+        for (int i = 0; i < GRD; ++i) guards += (a[i] != SENT) + (a[a.size() - 1 - i] != SENT);
+    }
+    for (int s = 0; s < NS3; ++s) nonfinite += !std::isfinite(y[s]) || std::fabs(y[s]) > 1e100;
+    for (int s = 0; s < NS3; ++s) {
+        err = std::max(err, std::fabs(y[s] - yr[s]));
+        nrm = std::max(nrm, std::fabs(yr[s]));
+        if (writes[s] != 1) ++bad_writes;
+    }
+    printf("D1=%d TT=%d threads=%d  max|y-yref|/max|yref| = %.3e  slots written != once: %d  guards hit: %d  "
+           "non-finite: %d\n", D1, TT, NT, err / nrm, bad_writes, guards, nonfinite);
+    return (bad_writes == 0 && guards == 0 && nonfinite == 0 && err / nrm < 1e-13) ? 0.0 : 1.0;
+}
+
+int main()
+{
+    double bad = 0;
+    bad += run<2, 4>(1); bad += run<3, 3>(2); bad += run<4, 2>(3); bad += run<5, 2>(4); bad += run<6, 2>(5);
+    bad += run<7, 1>(6); bad += run<2, 1>(7); bad += run<3, 2>(8); bad += run<4, 1>(9); bad += run<5, 1>(10);
+    printf(bad == 0 ? "ALL OK\n" : "FAILURES\n");
+    return bad == 0 ? 0 : 1;
+}
