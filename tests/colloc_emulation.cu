@@ -113,6 +113,18 @@ double run(unsigned seed)
     return (bad_writes == 0 && guards == 0 && nonfinite == 0 && err / nrm < 1e-13) ? 0.0 : 1.0;
 }
 
+// The FP32 tile variants that load the last stage's slot codes from global memory: those whose
+// shared-memory-limited CTAs per SM rise without the codes.  Single-instance kernel: orders 3-6
+// (9 -> 10, 4 -> 5, 2 -> 3, 12 -> 14 CTAs per SM), not orders 1-2.  Batch variants: the order-4
+// one-element tile (28 -> 32), not the other small ones (already at 16 or 32).
+static_assert(!TileShape2<2, 4>::LATE_CODES && !TileShape2<3, 3>::LATE_CODES, "orders 1-2 keep shared-memory codes");
+static_assert(TileShape2<4, 2>::LATE_CODES && TileShape2<5, 2>::LATE_CODES && TileShape2<6, 2>::LATE_CODES &&
+                  TileShape2<7, 1>::LATE_CODES,
+              "orders 3-6 load late codes");
+static_assert(!TileShape2<2, 2>::LATE_CODES && !TileShape2<3, 2>::LATE_CODES && !TileShape2<3, 1>::LATE_CODES &&
+                  !TileShape2<4, 1>::LATE_CODES && TileShape2<5, 1>::LATE_CODES,
+              "batch variants: only the order-4 one-element tile loads late codes");
+
 int main()
 {
     double bad = 0;
