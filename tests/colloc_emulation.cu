@@ -5,7 +5,8 @@
 // work array sits between guard regions (an access outside reads a huge sentinel or overwrites
 // one) and starts as NaN (a read of an unwritten entry shows in the result).  Checks, per tile
 // shape: agreement with the reference to 1e-13 of its largest entry, every slot written exactly
-// once, no guard touched, every output finite.  Exit status 0 when all shapes pass.
+// once, no guard touched, every output finite.  Also: the collocation derivative table is exact on
+// polynomials of degree < Q1.  Exit status 0 when everything passes.
 #include "element_kernels.cuh"
 #include <cstdio>
 #include <cmath>
@@ -125,9 +126,30 @@ static_assert(!TileShape2<2, 2>::LATE_CODES && !TileShape2<3, 2>::LATE_CODES && 
                   !TileShape2<4, 1>::LATE_CODES && TileShape2<5, 1>::LATE_CODES,
               "batch variants: only the order-4 one-element tile loads late codes");
 
+// The collocation derivative on Q1 Gauss points is exact on polynomials of degree < Q1: for
+// p(x) = x^m, sum_j Dc[q][j] p(x_j) = m x_q^(m-1) at every Gauss point (x on [0, 1]).
+double check_dc(int q1)
+{
+    std::vector<double> gx, gw, xq(q1), cval, cder;
+    gauss_legendre(q1, gx, gw);
+    for (int q = 0; q < q1; ++q) xq[q] = 0.5 * (gx[q] + 1.0);
+    lagrange_tables(xq, xq, cval, cder);
+    double worst = 0.0;
+    for (int m = 0; m < q1; ++m)
+        for (int q = 0; q < q1; ++q) {
+            double d = 0.0;
+            for (int j = 0; j < q1; ++j) d += cder[q * q1 + j] * std::pow(xq[j], m);
+            const double exact = m == 0 ? 0.0 : m * std::pow(xq[q], m - 1);
+            worst = std::max(worst, std::fabs(d - exact));
+        }
+    printf("Q1=%d collocation derivative: max error on x^m, m < Q1: %.3e\n", q1, worst);
+    return worst < 1e-12 ? 0.0 : 1.0;
+}
+
 int main()
 {
     double bad = 0;
+    for (int q1 = 2; q1 <= 7; ++q1) bad += check_dc(q1);
     bad += run<2, 4>(1); bad += run<3, 3>(2); bad += run<4, 2>(3); bad += run<5, 2>(4); bad += run<6, 2>(5);
     bad += run<7, 1>(6); bad += run<2, 1>(7); bad += run<3, 2>(8); bad += run<4, 1>(9); bad += run<5, 1>(10);
     printf(bad == 0 ? "ALL OK\n" : "FAILURES\n");
