@@ -44,7 +44,8 @@
 
 /* ORC_PLANT (default 0) compiles a deliberately wrong variant so that the test suite can show its
  * pins catch the mistake: 1 drops the (p-2) g g^T term of the tangent, 2 uses J^{-1} where
- * J^{-T} belongs, 3 flips the sign of the source term, 4 swaps two Gauss weights. */
+ * J^{-T} belongs, 3 flips the sign of the source term, 4 swaps two Gauss weights, 5 takes eps for
+ * eps^2 in the regularised law (residual and tangent alike). */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
 #endif
@@ -342,7 +343,7 @@ static void law(const orc_problem *P, double kr, const double *g, double *flux, 
     int dim = P->dim;
     double s = 0.0;
     for (int d = 0; d < dim; ++d) s += g[d] * g[d];
-    double base = P->eps * P->eps + s;
+    double base = (ORC_PLANT == 5 ? P->eps : P->eps * P->eps) + s;
     double kap, kap2;
     if (base == 0.0) {
         kap = (P->p == 2.0) ? 1.0 : 0.0;

@@ -109,6 +109,42 @@ def test_patch_detects_nonlinear_field():
     assert np.abs(r).max() > 1e-3
 
 
+# ------------------------------------------------------ the regularised law (eps > 0)
+
+@pytest.mark.parametrize("dim,n,k", [(2, 3, 2), (3, 2, 2)])
+@pytest.mark.parametrize("p,eps", [(1.5, 0.5), (2.5, 0.3), (3.0, 1e-2), (4.0, 0.5)])
+def test_patch_linear_field_regularised(dim, n, k, p, eps):
+    """eps > 0: the flux of a linear field a.x + b is still constant, (eps^2 + |a|^2)^((p-2)/2) a,
+    so interior R = 0, and the flux work over the unit box is exactly
+    (eps^2 + |a|^2)^((p-2)/2) |a|^2 (an eps-for-eps^2 slip changes it)."""
+    V = I.lattice_vertices(dim, n, seed=11)
+    P = O.Problem(dim, n, k, V, p=p, eps=eps, f_const=0.0)
+    x = O.node_coords(P)
+    a = np.array([0.3, -0.7, 0.5])[:dim]
+    u = x @ a + 0.2
+    assert np.abs(O.residual(P, u)).max() < 2e-14
+    a2 = float(a @ a)
+    expect = (eps * eps + a2) ** ((p - 2.0) / 2.0) * a2
+    assert abs(O.flux_work(P, u) - expect) < 1e-12 * expect
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 4, 2), (3, 2, 3)])
+@pytest.mark.parametrize("p,eps", [(1.5, 0.5), (3.0, 0.5), (2.5, 1e-2)])
+def test_symmetry_and_fd_regularised(dim, n, k, p, eps):
+    """eps > 0 (including p < 2): J is symmetric and central differences of R match J v."""
+    V = I.lattice_vertices(dim, n, seed=0)
+    P = O.Problem(dim, n, k, V, p=p, eps=eps)
+    u = I.smooth_field(dim, n, k, seed=1)
+    ess = O.essential(P)
+    v = I.uniform_vector(P.n_dofs, seed=2); v[ess] = 0.0
+    w = I.uniform_vector(P.n_dofs, seed=3); w[ess] = 0.0
+    Jv, Jw = O.jv(P, u, v), O.jv(P, u, w)
+    assert abs(w @ Jv - v @ Jw) <= 1e-13 * abs(w @ Jv)
+    h = 1e-5 * np.linalg.norm(u) / np.linalg.norm(v)
+    fd = (O.residual(P, u + h * v) - O.residual(P, u - h * v)) / (2 * h)
+    assert np.linalg.norm(fd - Jv) <= 1e-7 * np.linalg.norm(Jv)
+
+
 # ----------------------------------------------------------------------- p = 2 Laplacian
 
 def _exact_1d(k):
@@ -219,6 +255,10 @@ def _pins_hold() -> list[str]:
         failed.append("kronecker")
     if abs(O.load(O.Problem(2, 3, 2, V, p=3.0)).sum() - 1.0) > 1e-13:
         failed.append("load")
+    P = O.Problem(2, 3, 2, V, p=1.5, eps=0.5, f_const=0.0)
+    a = np.array([0.3, -0.7])
+    if abs(O.flux_work(P, O.node_coords(P) @ a) - (0.25 + a @ a) ** -0.25 * (a @ a)) > 1e-12:
+        failed.append("eps")
     P = O.Problem(2, 4, 2, I.lattice_vertices(2, 4, seed=0), p=3.0)
     u = I.smooth_field(2, 4, 2, seed=1)
     v = I.uniform_vector(P.n_dofs, seed=2); v[O.essential(P)] = 0.0
@@ -234,7 +274,7 @@ def test_pins_hold_for_the_oracle():
     assert _pins_hold() == []
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5])
 def test_pins_catch_planted_mistakes(plant):
     """Build the oracle with a deliberate slip and check that some pin fails."""
     with O.planted(plant):
@@ -309,9 +349,16 @@ def test_adjoint_homogeneity():
         u, hist = O.newton(P, I.smooth_field(2, 4, 2, seed=1), rtol=1e-14)
         lam = O.adjoint_solve(P, u)
         np.testing.assert_allclose(lam, u / (p - 1.0), atol=1e-10 * np.abs(u).max())
-        # closed form of the gradient: -kappa'(rho_e)/(p-1) int_e kappa |grad u|^2
+        # closed form of the gradient: g_e = lambda^T dR/drho_e = kappa'(rho_e)/(p-1) int_e |grad u|^p
+        # (the compliance gradient is -g); int_e |grad u|^p is the flux work of a problem whose design
+        # factor is the indicator of element e (kappa_eps = 0, q = 1)
         g = O.adjoint_grad(P, u, lam)
-        assert np.all(g > 0)
+        dk = P.kappa_q * P.rho ** (P.kappa_q - 1.0)
+        work = np.array([O.flux_work(O.Problem(P.dim, P.n, P.order, P.vertices, p=p,
+                                                rho=np.eye(P.n_elems)[e], kappa_eps=0.0, kappa_q=1.0), u)
+                         for e in range(P.n_elems)])
+        assert np.all(work > 0)
+        np.testing.assert_allclose(g, dk / (p - 1.0) * work, rtol=1e-8)
 
 
 def test_adjoint_against_central_differences():
