@@ -1,10 +1,12 @@
 """Benchmark of the matrix-free p-Laplacian Jacobian action and Newton-CG solve on one GB300.
 
 Workload: 3D p-Laplacian p=3 on a 64^3 hex lattice with seeded jitter, order 3 (7,189,057 DOFs),
-4^3 Gauss points per element, linearised at the seeded smooth state.  One timed step is one
-partially assembled Jacobian action y = J(u) v in FP32 (the operator the mixed-precision CG
-applies); the FP64 action, the FP64 residual and the full Newton-CG solves (FP64 and mixed
-precision, to 1e-8 relative residual) are measured in the same run and reported beside it.
+4^3 Gauss points per element, linearised at the seeded smooth state, FP64.  One timed step is one
+partially assembled Jacobian action y = J(u) v in FP64 (Eq. 2), the headline `value`, graded
+against the measured FP64 fused multiply-add rate.  Measured in the same run and reported beside
+it: the FP32 action (the operator the mixed-precision CG applies) with its HBM roofline, the
+double-float action, the FP64 residual, the FP64 action end to end through host buffers, and the
+full Newton-CG solves (FP64 and mixed precision, to 1e-8 relative residual).
 
 Prints one JSON line.  ``--impl reference`` times the oracle (plain FP64 C on the host cores) on
 a bounded sample of the same workload instead.  Under torchrun every rank runs an independent
@@ -136,6 +138,33 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+FP64_NOMINAL_TFLOPS = 1.25   # nominal dense FP64 rate of the GB300 (context only)
+FP64_PEAK_FILE = os.path.join(ROOT, "profiles", "fp64_peak.json")
+
+
+def fp64_peak() -> dict:
+    """The FP64 rate the FP64 kernels are graded against: the committed measurement of this GPU
+    model's FMA rate (written by ``bench.py --suite fp64-peak``), else the nominal figure."""
+    if os.path.exists(FP64_PEAK_FILE):
+        d = json.load(open(FP64_PEAK_FILE))
+        return {"tflops": float(d["tflops_best"]), "source": "measured (profiles/fp64_peak.json)"}
+    return {"tflops": FP64_NOMINAL_TFLOPS, "source": "nominal"}
+
+
+def jv_algorithmic_flops(dim: int, n_e: int, d1: int, q1: int) -> float:
+    """Flops of one partially assembled J v: per element, interpolation plus collocated gradient
+    in both directions (4 d D1^(d+1) multiply-adds) and the symmetric d x d matvec per point."""
+    return 2.0 * n_e * (4 * dim * d1 ** (dim + 1) + dim * dim * q1 ** dim)
+
+
+def residual_algorithmic_flops(dim: int, n_e: int, d1: int, q1: int) -> float:
+    """Flops of one residual R(u): the same contractions as J v (4 d D1^(d+1) multiply-adds per
+    element) plus, per point, M g (d^2 multiply-adds), g . M g / (w det J) (d + 1) and the flux
+    kappa M g (d multiplies); the power kappa = (eps^2 + sigma)^((p-2)/2) is not counted."""
+    per_point = 2 * dim * dim + 2 * (dim + 1) + dim
+    return 2.0 * n_e * 4 * dim * d1 ** (dim + 1) + n_e * q1 ** dim * per_point
+
+
 def jv_algorithmic_bytes(n_l: int, n_e: int, nq_per_elem: int, nl_per_elem: int, word: int) -> int:
     """Bytes a partially assembled J v must move: read v and write y (N_L words each), read the
     6 symmetric tangent entries per quadrature point, read the element index (4 B per E-vector
@@ -177,6 +206,7 @@ def run_gpu(args) -> dict | None:
     import torch.distributed as dist
 
     from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import abi
     from paper_2506_00746_gb300 import inputs as I
 
     world, rank, local = dist_env()
@@ -198,6 +228,7 @@ def run_gpu(args) -> dict | None:
     stream = torch.cuda.current_stream()
 
     def timed(fn, steps, warmup):
+        """K calls between barriers and synchronisations, CUDA events on the launching stream."""
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
@@ -213,52 +244,76 @@ def run_gpu(args) -> dict | None:
         barrier(dev)
         return e0.elapsed_time(e1) / 1e3, op.launch_count() - l0
 
-    # ---- headline: FP32 Jacobian action, device-resident inputs ----
-    jv32 = lambda: op.jacobian_action(v32, precision=32, out=y32)
+    def call_median(fn, calls):
+        """Median of `calls` individually event-timed calls (ms)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    def kernel_ms(fn, calls):
+        """Per-kernel average durations (ms) from the library's own events around each launch."""
+        op.prof_enable(True)
+        op.prof_reset()
+        for _ in range(calls):
+            fn()
+        prof = op.prof_read()
+        op.prof_enable(False)
+        return {k: ms / n for k, (n, ms) in prof.items() if n > 0}
+
+    ncalls = max(50, args.steps)
+
+    # ---- headline: FP64 partially assembled Jacobian action, device-resident inputs ----
+    jv64 = lambda: op.jacobian_action(v64, precision=64, out=y64)
     clk = ClockSampler(local).start()
-    t_dev, launches = timed(jv32, args.steps, args.warmup)
+    t_dev, launches = timed(jv64, args.steps, args.warmup)
     clocks = clk.stop()
     value, t_max = aggregate(nl * args.steps / 1e9, t_dev, world, dev)
+    med64 = call_median(jv64, ncalls)
+    k64 = kernel_ms(jv64, ncalls)
+    t_main64 = k64.get("jv_pa_f64", float("nan")) / 1e3
+    t_fix64 = k64.get("fixup", 0.0) / 1e3
+    y64_host = y64.cpu().numpy() if rank == 0 else None
 
-    # ---- per-kernel durations over the same kind of timed region (library CUDA events) ----
-    op.prof_enable(True)
-    op.prof_reset()
-    for _ in range(args.steps):
-        jv32()
-    prof = op.prof_read()
-    op.prof_enable(False)
-    main_n, main_ms = prof.get("jv_pa_f32", (1, float("nan")))
-    fix_n, fix_ms = prof.get("fixup", (0, 0.0))
-    t_main = main_ms / 1e3 / max(main_n, 1)
-    t_fix = fix_ms / 1e3 / max(fix_n, 1) if fix_n else 0.0
+    # ---- the FP32 action (inner operator of the mixed-precision CG): HBM roofline ----
+    jv32 = lambda: op.jacobian_action(v32, precision=32, out=y32)
+    t32, l32 = timed(jv32, ncalls, args.warmup)
+    med32 = call_median(jv32, ncalls)
+    k32 = kernel_ms(jv32, ncalls)
+    t_main32 = k32.get("jv_pa_f32", float("nan")) / 1e3
+    t_fix32 = k32.get("fixup", 0.0) / 1e3
+    y32_host = y32.double().cpu().numpy() if rank == 0 else None
 
     # ---- other operators of the path ----
-    jv64 = lambda: op.jacobian_action(v64, precision=64, out=y64)
-    t64, _ = timed(jv64, max(3, args.steps // 20), 2)
-    n64 = max(3, args.steps // 20)
-    # double-float operator (FP32 word pairs): the first call splits the FP64 tangent, untimed
     jvdf = lambda: op.jacobian_action(v64, precision=48, out=y64)
-    jvdf()
-    tdf, _ = timed(jvdf, max(3, args.steps // 10), 2)
-    ndf = max(3, args.steps // 10)
+    jvdf()                       # splits the FP64 tangent into word pairs (once per linearisation)
+    tdf, _ = timed(jvdf, ncalls, 3)
+    ydf_host = y64.cpu().numpy() if rank == 0 else None
     jvcg = lambda: op.jacobian_action(v64, precision=-32, out=y64)
-    tcg, _ = timed(jvcg, args.steps, 3)
+    tcg, _ = timed(jvcg, ncalls, 3)
     r = torch.empty_like(u0)
     res = lambda: op.residual(u0, out=r)
-    nres = max(3, args.steps // 20)
-    tres, _ = timed(res, nres, 2)
+    tres, _ = timed(res, ncalls, 3)
+    kres = kernel_ms(res, 10)
+    t_res_main = kres.get("residual", float("nan")) / 1e3
+    r_host = r.cpu().numpy() if rank == 0 else None
+    f64peak = fp64_peak()
+    live_best, live_med = abi.fe_measure_fp64_peak(10)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region) ----
-    vh = v32.cpu().pin_memory()
+    vh = v64.cpu().pin_memory()
     yh = torch.empty_like(vh).pin_memory()
     for _ in range(3):
-        op.jacobian_action_host(vh, yh, precision=32)
+        op.jacobian_action_host(vh, yh, precision=64)
     torch.cuda.synchronize()
     barrier(dev)
-    ne2e = max(5, args.steps // 4)
+    ne2e = max(5, args.steps)
     t0 = time.perf_counter()
     for _ in range(ne2e):
-        op.jacobian_action_host(vh, yh, precision=32)
+        op.jacobian_action_host(vh, yh, precision=64)
     t_e2e = time.perf_counter() - t0
     e2e_value, _ = aggregate(nl * ne2e / 1e9, t_e2e, world, dev)
 
@@ -280,6 +335,8 @@ def run_gpu(args) -> dict | None:
                             "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
                             "rel_residual": rep["rel"], "cg_time_s": round(rep["cg_ms"] / 1e3, 4),
                             "kernel_launches": rep["launches"]}
+            if name == "mixed":
+                u_mixed_host = u.cpu().numpy() if rank == 0 else None
         for name, _ in NEWTON_MODES[:-1]:
             if "fp64" in newton and name in newton:
                 newton[f"speedup_{name}_vs_fp64"] = round(newton["fp64"]["time_s"] / newton[name]["time_s"], 3)
@@ -299,33 +356,24 @@ def run_gpu(args) -> dict | None:
         for name, _ in NEWTON_MODES[:-1]:
             ew[f"speedup_{name}_vs_fp64"] = round(ew["fp64"]["time_s"] / ew[name]["time_s"], 3)
         newton["eisenstat_walker"] = ew
-        # the small 2D configuration (16x16 quads, order 2), FP64 and mixed, beside the oracle's
-        w2 = I.WORKLOADS["2d_p3_k2_16x16"]
-        op2 = Operator(2, w2.n, w2.order, I.lattice_vertices(2, w2.n, seed=w2.mesh_seed), p=w2.p, eps=w2.eps)
-        u2 = torch.from_numpy(I.smooth_field(2, w2.n, w2.order, seed=w2.state_seed)).cuda()
-        small = {}
-        for name, prec in (("mixed", -32), ("fp64", 64)):
-            uu = u2.clone()
-            op2.newton_solve(uu, rtol=1e-8, inner_precision=prec)        # warm-up (graph creation)
-            uu = u2.clone()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rep = op2.newton_solve(uu, rtol=1e-8, inner_precision=prec, raise_on_error=False)
-            torch.cuda.synchronize()
-            small[name] = {"time_s": round(time.perf_counter() - t0, 5), "status": rep["status"],
-                           "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"]}
-        op2.close()
-        newton["2d_16x16_order2"] = small
+        newton["small_cases"] = small_newton_cases(Operator, I)
+    else:
+        u_mixed_host = None
 
     if rank != 0:
         op.close()
         return None
 
     peaks = measured_peaks()
-    bytes_alg = jv_algorithmic_bytes(nl, ne, nq, nq, 4)
-    achieved = bytes_alg / t_main / 1e9
-    kname = "k_jv_tile2<4,2,float>"
-    traffic, traffic_src = profiled_traffic(kname)
+    flops64 = jv_algorithmic_flops(w.dim, ne, w.order + 1, w.order + 1)
+    achieved64 = flops64 / t_main64 / 1e12
+    k64name = "k_jv_tile<4,2,double,double>"
+    traffic64, traffic64_src = profiled_traffic(k64name)
+    bytes64 = jv_algorithmic_bytes(nl, ne, nq, nq, 8)
+    bytes32 = jv_algorithmic_bytes(nl, ne, nq, nq, 4)
+    k32name = "k_jv_tile2<4,2,float>"
+    traffic32, traffic32_src = profiled_traffic(k32name)
+    flops_res = residual_algorithmic_flops(w.dim, ne, w.order + 1, w.order + 1)
     out = {
         "metric": METRIC,
         "value": round(value, 4),
@@ -337,50 +385,84 @@ def run_gpu(args) -> dict | None:
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f64",
         "data": "synthetic (seeded jittered lattice, seeded smooth state, seeded U[-1,1] direction)",
         "config": {"workload": f"{args.workload}: 3D p-Laplacian p=3, 64^3 hex, order 3, 4^3 Gauss points, "
-                               f"{nl} DOFs; step = one FP32 partially assembled J(u) v",
+                               f"{nl} DOFs; step = one FP64 partially assembled J(u) v",
                    "n_dofs": nl, "n_elements": ne, "order": w.order, "p": w.p,
-                   "l2": "inputs larger than L2 (FP32 tangent %.0f MB + index/vectors)" % (6 * 4 * ne * nq / 1e6),
+                   "l2": "inputs larger than L2 (FP64 tangent %.0f MB + index/vectors)" % (6 * 8 * ne * nq / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    # the library's default tile edge of 3D order k (elements per CTA = tile^3)
                    "tile": {1: 4, 2: 3, 3: 2, 4: 2, 5: 2, 6: 1}[w.order]},
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                     "kernel": kname, "peak_source": peaks["source"],
-                     "algorithmic_bytes_per_launch": bytes_alg,
-                     "kernel_ms": round(t_main * 1e3, 5), "fixup_ms": round(t_fix * 1e3, 5),
-                     "traffic_summary": traffic_src},
-        "e2e": {"value": round(e2e_value, 4), "unit": "GDOF/s", "h2d_bytes_per_step": 4 * nl,
-                "d2h_bytes_per_step": 4 * nl},
-        "jv_f64_gdofs": round(nl * n64 / t64 / 1e9, 4),
-        "jv_double_float_gdofs": round(nl * ndf / tdf / 1e9, 4),
-        "jv_cg_mixed_gdofs": round(nl * args.steps / tcg / 1e9, 4),
-        "residual_f64_gdofs": round(nl * nres / tres / 1e9, 4),
+        "roofline": {"bound": "fp64", "achieved": round(achieved64, 4), "peak": round(f64peak["tflops"], 4),
+                     "unit": "TFLOP/s", "frac": round(achieved64 / f64peak["tflops"], 4), "traffic": traffic64,
+                     "kernel": k64name, "peak_source": f64peak["source"],
+                     "peak_live_best_tflops": round(live_best, 4), "peak_live_median_tflops": round(live_med, 4),
+                     "algorithmic_flops_per_launch": flops64, "algorithmic_bytes_per_launch": bytes64,
+                     "kernel_ms": round(t_main64 * 1e3, 5), "fixup_ms": round(t_fix64 * 1e3, 5),
+                     "hbm_frac": round(bytes64 / t_main64 / 1e9 / peaks["hbm_gbs"], 4),
+                     "action_frac": round(flops64 / (t_dev / args.steps) / 1e12 / f64peak["tflops"], 4),
+                     "call_ms_median": round(med64, 5), "traffic_summary": traffic64_src},
+        "e2e": {"value": round(e2e_value, 4), "unit": "GDOF/s", "h2d_bytes_per_step": 8 * nl,
+                "d2h_bytes_per_step": 8 * nl},
+        "jv_f32": {"gdofs": round(nl * ncalls / t32 / 1e9, 4), "ms_per_action": round(t32 / ncalls * 1e3, 5),
+                   "call_ms_median": round(med32, 5), "launches_per_action": l32 / ncalls,
+                   "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                                "peak_source": peaks["source"], "kernel": k32name,
+                                "algorithmic_bytes_per_launch": bytes32,
+                                "kernel_ms": round(t_main32 * 1e3, 5), "fixup_ms": round(t_fix32 * 1e3, 5),
+                                "kernel_achieved": round(bytes32 / t_main32 / 1e9, 1),
+                                "kernel_frac": round(bytes32 / t_main32 / 1e9 / peaks["hbm_gbs"], 4),
+                                "action_frac": round(bytes32 / (t32 / ncalls) / 1e9 / peaks["hbm_gbs"], 4),
+                                "traffic": traffic32, "traffic_summary": traffic32_src}},
+        "jv_double_float_gdofs": round(nl * ncalls / tdf / 1e9, 4),
+        "jv_cg_mixed_gdofs": round(nl * ncalls / tcg / 1e9, 4),
+        "residual_f64": {"gdofs": round(nl * ncalls / tres / 1e9, 4), "kernel_ms": round(t_res_main * 1e3, 5),
+                         "algorithmic_flops": flops_res,
+                         "fp64_frac": round(flops_res / t_res_main / 1e12 / f64peak["tflops"], 4)},
         "newton": newton,
-        "kernel_ms": {k: round(ms / max(n, 1), 5) for k, (n, ms) in prof.items()},
+        "kernel_ms": {"f64": {k: round(v, 5) for k, v in k64.items()},
+                      "f32": {k: round(v, 5) for k, v in k32.items()}},
     }
     op.close()
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+        gpu = {"r": r_host, "jv_f64": y64_host, "jv_f32": y32_host, "jv_double_float": ydf_host,
+               "newton_mixed_u": u_mixed_host}
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds, gpu)
+    return out
+
+
+def small_newton_cases(Operator, I) -> dict:
+    """Newton solves of the small configurations whose oracle Newton the CPU baseline also times:
+    the 2D 16x16 order-2 problem and the 3D 16^3 order-2 problem, FP64 and mixed."""
+    import torch
+    out = {}
+    for key in ("2d_p3_k2_16x16", "3d_p3_k2_16"):
+        wk = I.WORKLOADS[key]
+        opk = Operator(wk.dim, wk.n, wk.order, I.lattice_vertices(wk.dim, wk.n, seed=wk.mesh_seed), p=wk.p,
+                       eps=wk.eps)
+        uk = torch.from_numpy(I.smooth_field(wk.dim, wk.n, wk.order, seed=wk.state_seed)).cuda()
+        small = {}
+        for name, prec in (("mixed", -32), ("fp64", 64)):
+            uu = uk.clone()
+            opk.newton_solve(uu, rtol=1e-8, inner_precision=prec)        # warm-up (graph creation)
+            uu = uk.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = opk.newton_solve(uu, rtol=1e-8, inner_precision=prec, raise_on_error=False)
+            torch.cuda.synchronize()
+            small[name] = {"time_s": round(time.perf_counter() - t0, 5), "status": rep["status"],
+                           "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"]}
+        opk.close()
+        out[key] = small
     return out
 
 
 # ------------------------------------------------------------------------------------------------
 # measurement suites beside the headline: the order sweep and the design-sensitivity case
 # ------------------------------------------------------------------------------------------------
-FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 rate of the GB300 (no measured FP64 peak is recorded)
-
-
-def jv_algorithmic_flops(dim: int, n_e: int, d1: int, q1: int) -> float:
-    """Flops of one partially assembled J v: per element, interpolation plus collocated gradient
-    in both directions (4 d D1^(d+1) multiply-adds) and the symmetric d x d matvec per point."""
-    return 2.0 * n_e * (4 * dim * d1 ** (dim + 1) + dim * dim * q1 ** dim)
-
-
 def _event_time(fn, steps: int, warmup: int) -> float:
     import torch
     for _ in range(warmup):
@@ -421,6 +503,7 @@ def run_sweep(args) -> dict:
     from paper_2506_00746_gb300 import inputs as I
     torch.cuda.set_device(0)
     peaks = measured_peaks()
+    f64 = fp64_peak()
     orders = [int(k) for k in args.orders.split(",")]
     rows = []
     clk = ClockSampler(0).start()
@@ -452,7 +535,7 @@ def run_sweep(args) -> dict:
                "jv_f32_main_kernel_ms": round(t_main * 1e3, 4),
                "jv_f32_hbm_frac": round(b32 / t_main / 1e9 / peaks["hbm_gbs"], 4),
                "jv_f64_gdofs": round(nl / t64 / 1e9, 3),
-               "jv_f64_fp64_frac": round(fl / t64 / 1e12 / FP64_PEAK_TFLOPS, 4),
+               "jv_f64_fp64_frac": round(fl / t64 / 1e12 / f64["tflops"], 4),
                "jv_double_float_gdofs": round(nl / tdf / 1e9, 3),
                "residual_f64_gdofs": round(nl / tres / 1e9, 3)}
         if not args.no_newton:
@@ -464,7 +547,7 @@ def run_sweep(args) -> dict:
     clocks = clk.stop()
     return {"suite": "sweep", "workload": "3D p-Laplacian p=3, orders %s, k n ~ 200 (about 8M DOFs)" % args.orders,
             "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"],
-            "fp64_peak_tflops": FP64_PEAK_TFLOPS, "fp64_peak_source": "nominal",
+            "fp64_peak_tflops": f64["tflops"], "fp64_peak_source": f64["source"],
             "jv_f32_hbm_frac_note": "algorithmic bytes (v, y, 6 tangent words per point, 4 B index per "
                                     "E-vector entry) / main kernel time, fix-up excluded",
             "clocks": clocks, "orders": rows}
@@ -647,6 +730,32 @@ def run_element_ad(args) -> dict:
     return {"suite": "element-ad", "note": "dense element tangents; one CTA loops over elements", "orders": rows}
 
 
+def run_fp64_peak(args) -> dict:
+    """The FP64 fused multiply-add rate of this GPU (fe_measure_fp64_peak: independent FMA chains on
+    every SM, CUDA events), with the SM clocks sampled while it runs."""
+    import torch
+
+    from paper_2506_00746_gb300 import abi
+    torch.cuda.set_device(0)
+    clk = ClockSampler(0).start()
+    runs = [abi.fe_measure_fp64_peak(args.reps) for _ in range(5)]
+    clocks = clk.stop()
+    best = max(b for b, _ in runs)
+    out = {"suite": "fp64-peak", "gpu": torch.cuda.get_device_name(0), "tflops_best": round(best, 4),
+            "tflops_median_per_run": [round(m, 4) for _, m in runs], "reps_per_run": args.reps,
+            "sm_count": torch.cuda.get_device_properties(0).multi_processor_count, "clocks": clocks,
+            "fma_per_clk_per_sm": (round(best * 1e12 / 2 / torch.cuda.get_device_properties(0).multi_processor_count
+                                         / (clocks["sm_mhz"] * 1e6), 3) if clocks.get("sm_mhz") else None),
+            "method": "16 independent FP64 FMA chains per thread, 256-thread CTAs, every SM filled to its "
+                      "occupancy, 4096 iterations per launch; 2 untimed launches, then `reps` timed ones",
+           "command": "python bench.py --suite fp64-peak --reps %d" % args.reps}
+    if args.save:
+        os.makedirs(os.path.dirname(os.path.abspath(args.save)), exist_ok=True)
+        with open(args.save, "w") as f:
+            json.dump(out, f, indent=1)
+    return out
+
+
 def run_jv_small(args) -> dict:
     """A few Jacobian actions of one 3D p=3 instance (the small cases the ncu captures use): n
     elements per direction, order, precision 64 / 32 / -32, `reps` actions after linearising at
@@ -698,9 +807,13 @@ def run_batch_subset(args) -> dict:
 # ------------------------------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline / reference arm)
 # ------------------------------------------------------------------------------------------------
-def cpu_baseline(workload: str, budget_s: float = 12.0) -> dict:
-    """Oracle J v (element by element, FP64, OpenMP over element colours) on a bounded sample of
-    the elements of the workload, scaled to GDOF/s of a whole action."""
+def cpu_baseline(workload: str, budget_s: float = 12.0, gpu: dict | None = None) -> dict:
+    """The oracle on the host cores: its FP64 J v and R (element by element, OpenMP over element
+    colours) on the workload -- the whole vector when that fits the budget, else a bounded sample
+    of the elements, scaled to GDOF/s of a whole action -- and the Newton solves of the small
+    configurations.  With the GPU's results of the same inputs (`gpu`), the relative 2-norm
+    error of each against the oracle's whole-vector result, and the oracle's residual of the
+    GPU's mixed-precision Newton solution."""
     import numpy as np
 
     import oracle as O
@@ -711,39 +824,68 @@ def cpu_baseline(workload: str, budget_s: float = 12.0) -> dict:
     u = I.smooth_field(w.dim, w.n, w.order, seed=w.state_seed)
     v = I.uniform_vector(P.n_dofs, seed=w.dir_seed)
     cores = O.set_threads(os.cpu_count() or 1)
-    y = np.zeros(P.n_dofs)
-    m = max(1, P.n_elems // 512)
-    t0 = time.perf_counter()
-    O.jv_partial(P, u, v, 0, m, y)
-    dt = time.perf_counter() - t0
-    m = int(min(P.n_elems, max(m, m * budget_s / max(dt, 1e-6))))
-    t0 = time.perf_counter()
-    O.jv_partial(P, u, v, 0, m, y)
-    dt = time.perf_counter() - t0
+
+    def sample(fn, share):
+        """(elements timed, seconds): a probe on 1/512 of the elements, then as many as the
+        budget share allows (all of them when they fit)."""
+        m = max(1, P.n_elems // 512)
+        t0 = time.perf_counter()
+        fn(m)
+        dt = time.perf_counter() - t0
+        m = int(min(P.n_elems, max(m, m * share * budget_s / max(dt, 1e-6))))
+        t0 = time.perf_counter()
+        fn(m)
+        return m, time.perf_counter() - t0
+
+    m, dt = sample(lambda mm: O.jv_partial(P, u, v, 0, mm), 0.4)
     value = P.n_dofs * (m / P.n_elems) / dt / 1e9
-    # the residual on a sample timed the same way (half the budget)
-    r = np.zeros(P.n_dofs)
-    mr = max(1, P.n_elems // 512)
-    t0 = time.perf_counter()
-    O.residual_partial(P, u, 0, mr, r)
-    dtr = time.perf_counter() - t0
-    mr = int(min(P.n_elems, max(mr, mr * 0.5 * budget_s / max(dtr, 1e-6))))
-    t0 = time.perf_counter()
-    O.residual_partial(P, u, 0, mr, r)
-    dtr = time.perf_counter() - t0
-    # the small 2D configuration's Newton solve (sparse direct inner solves), whole
-    w2 = I.WORKLOADS["2d_p3_k2_16x16"]
-    P2 = O.Problem(w2.dim, w2.n, w2.order, I.lattice_vertices(w2.dim, w2.n, seed=w2.mesh_seed), p=w2.p, eps=w2.eps)
-    u2 = I.smooth_field(w2.dim, w2.n, w2.order, seed=w2.state_seed)
-    t0 = time.perf_counter()
-    O.newton(P2, u2, rtol=1e-8)
-    dtn = time.perf_counter() - t0
-    return {"value": round(value, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
-            "sample": f"element-by-element FP64 J(u) v over the first {m} of {P.n_elems} elements "
-                      f"({dt:.1f} s), scaled by the element fraction",
-            "residual_gdofs": round(P.n_dofs * (mr / P.n_elems) / dtr / 1e9, 6),
-            "residual_sample": f"FP64 R(u) over the first {mr} elements ({dtr:.1f} s), scaled likewise",
-            "newton_2d_16x16_s": round(dtn, 4)}
+    mr, dtr = sample(lambda mm: O.residual_partial(P, u, 0, mm), 0.2)
+    out = {"value": round(value, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+           "sample": f"element-by-element FP64 J(u) v over the first {m} of {P.n_elems} elements "
+                     f"({dt:.1f} s), scaled by the element fraction",
+           "residual_gdofs": round(P.n_dofs * (mr / P.n_elems) / dtr / 1e9, 6),
+           "residual_sample": f"FP64 R(u) over the first {mr} of {P.n_elems} elements ({dtr:.1f} s), scaled likewise"}
+    if gpu is not None:
+        # the oracle's whole-vector results (Dirichlet convention included) against the GPU's on
+        # the same inputs
+        y_ref = O.jv(P, u, v)
+        r_ref = O.residual(P, u)
+        v32 = v.astype(np.float32).astype(np.float64)
+        y_ref32 = O.jv(P, u, v32)
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        err = {}
+        if gpu.get("r") is not None:
+            err["residual_f64"] = rel(gpu["r"], r_ref)
+        if gpu.get("jv_f64") is not None:
+            err["jv_f64"] = rel(gpu["jv_f64"], y_ref)
+        if gpu.get("jv_double_float") is not None:
+            err["jv_double_float"] = rel(gpu["jv_double_float"], y_ref)
+        if gpu.get("jv_f32") is not None:
+            err["jv_f32"] = rel(gpu["jv_f32"], y_ref32)
+        if gpu.get("newton_mixed_u") is not None:
+            err["newton_mixed_oracle_rel_residual"] = float(
+                np.linalg.norm(O.residual(P, gpu["newton_mixed_u"])) / np.linalg.norm(r_ref))
+        out["err_vs_oracle"] = err
+        out["err_note"] = ("relative 2-norm over the whole vector; FP32 J v against the oracle's J v of the "
+                           "FP32-rounded direction; tolerances 1e-12 (FP64, double-float) and 1e-5 (FP32)")
+    # Newton solves of the small configurations: 2D 16x16 order 2 (sparse direct inner solves)
+    # and 3D 16^3 order 2 (Jacobi-preconditioned CG inner solves to 1e-4, as the GPU's)
+    newton = {}
+    for key, linear in (("2d_p3_k2_16x16", "direct"), ("3d_p3_k2_16", "cg")):
+        wk = I.WORKLOADS[key]
+        Pk = O.Problem(wk.dim, wk.n, wk.order, I.lattice_vertices(wk.dim, wk.n, seed=wk.mesh_seed), p=wk.p,
+                       eps=wk.eps)
+        uk = I.smooth_field(wk.dim, wk.n, wk.order, seed=wk.state_seed)
+        its: list = []
+        t0 = time.perf_counter()
+        _, hist = O.newton(Pk, uk, rtol=1e-8, linear=linear, cg_iters=its)
+        newton[key] = {"time_s": round(time.perf_counter() - t0, 4), "linear_solver": linear,
+                       "newton_iters": len(hist) - 1, "cg_iters": int(sum(its)) if its else None,
+                       "rel_residual": float(hist[-1] / hist[0])}
+    out["newton"] = newton
+    out["newton_note"] = ("the 64^3 order-3 oracle Newton is impractical on the host cores; the 48^3 design "
+                          "case's oracle solve is timed by the design suite")
+    return out
 
 
 def run_reference(args) -> dict | None:
@@ -798,7 +940,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-newton", type=int, default=50)
-    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "element-ad", "jv", "batch-subset"],
+    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "element-ad", "jv", "batch-subset",
+                                        "fp64-peak"],
                     default="headline",
                     help="headline (the benchmark line), sweep (orders 1-6), design (adjoint case), batched "
                          "(64 instances in one persistent launch); jv and batch-subset run the small cases "
@@ -810,12 +953,15 @@ def main(argv=None):
     ap.add_argument("--instances", type=int, default=24)
     ap.add_argument("--orders", default="1,2,3,4,5,6")
     ap.add_argument("--fd-dirs", type=int, default=20)
+    ap.add_argument("--save", default=None,
+                    help="fp64-peak: also write the result to this JSON file (profiles/fp64_peak.json is the "
+                         "committed copy the FP64 rooflines read)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.suite != "headline" and args.impl == "gpu":
         out = {"sweep": run_sweep, "design": run_design, "batched": run_batched, "element-ad": run_element_ad,
-               "jv": run_jv_small,
+               "jv": run_jv_small, "fp64-peak": run_fp64_peak,
                "batch-subset": run_batch_subset}[args.suite](args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -153,19 +153,19 @@ fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host,
 
 /* fe_jacobian_action_noalloc: the same y = J v as fe_jacobian_action with u == NULL (cached
  * linearisation, precision 64 / 32 / -32 with the same meaning; not 48, whose tangent storage
- * is allocated on first use), for callers that must not
- * allocate device memory while they run -- e.g. code executing while a stream capture in global
- * mode is active (cudaMalloc is not permitted there), or an application whose GPU memory is all
- * handed out by its own pool allocator, so that a cudaMalloc would fail or disturb the pool.
- * The paper has no counterpart; it is a deployment variant of the Jacobian action.
+ * is allocated on first use), for callers that cannot call cudaMalloc while they run: an
+ * application whose device memory is all handed out by its own pool allocator (a cudaMalloc would
+ * fail, or take memory the pool counts on), or a host loop with a latency budget that cannot absorb
+ * the device-wide synchronisation an allocation may cause.  The paper has no counterpart; it is a
+ * deployment variant of the Jacobian action.
  *
  * Scratch: the cross-tile partial sums that fe_jacobian_action keeps in the context's halo buffer
  * go instead to one file-scope device array of FE_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU
  * that loads the library holds until the process exits.  A problem needs one word (8 bytes for
  * precision 64, else 4) per cross-tile partial sum -- about 127 per tile for 3D order 3 with the
  * default 2^3-element tile, so up to about 64^3 elements in FP32 and 50^3 in FP64; larger
- * problems return FE_ERR_UNSUPPORTED with a message and launch nothing.  Every scratch entry that is read is written earlier in the
- * same call, so nothing needs clearing between calls.
+ * problems return FE_ERR_UNSUPPORTED with a message and launch nothing.  Every scratch entry that
+ * is read is written earlier in the same call, so nothing needs clearing between calls.
  *
  * The first call on a device resolves the array's device address (cudaGetSymbolAddress, with
  * that device current); make that first call before any stream capture.  All calls share the one
@@ -173,7 +173,7 @@ fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host,
  * and produce wrong results -- serialise them.  The call itself allocates nothing (no cudaMalloc,
  * cudaFree or allocating library routine).  v, y: device arrays as for fe_jacobian_action;
  * FE_ERR_STATE without a cached linearisation, FE_ERR_ARG if the current device is not the
- * context's. */
+ * context's or its index is beyond the 64 devices the address table covers. */
 #define FE_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 fe_status fe_jacobian_action_noalloc(fe_ctx *ctx, const void *v, void *y, int precision, void *stream);
 
@@ -293,6 +293,14 @@ fe_status fe_launch_count(const fe_ctx *ctx, int64_t *launches);
 
 /* Device bytes held by the context. */
 fe_status fe_memory_bytes(const fe_ctx *ctx, int64_t *bytes);
+
+/* fe_measure_fp64_peak: the FP64 fused multiply-add rate of the current device, measured (the
+ * paper has no counterpart: it is the denominator of the FP64-pipe roofline that the FP64
+ * operators are reported against).  A kernel of independent FMA chains fills every SM; it runs
+ * twice untimed, then `reps` times, each timed with CUDA events on `stream`.  *tflops_best and
+ * *tflops_median (may be NULL) receive 2 x FMAs / second / 1e12 of the fastest and the median
+ * launch.  Allocates and frees one small result array; synchronous.  FE_ERR_ARG for reps < 1. */
+fe_status fe_measure_fp64_peak(int reps, double *tflops_best, double *tflops_median, void *stream);
 
 void fe_destroy(fe_ctx *ctx);
 const char *fe_last_error(const fe_ctx *ctx);

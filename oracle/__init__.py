@@ -294,14 +294,22 @@ def exact_exp(dim: int, x):
 
 
 def newton(P: Problem, u0, rtol: float = 1e-8, max_newton: int = 60, armijo: float = 1e-4,
-           max_halvings: int = 20, history: list | None = None):
-    """Newton's method for R(u) = 0 with a sparse direct solve and backtracking on ||R||_2.
+           max_halvings: int = 20, history: list | None = None, linear: str = "direct",
+           cg_rtol: float = 1e-4, cg_iters: list | None = None):
+    """Newton's method for R(u) = 0 with backtracking on ||R||_2.
 
-    A step alpha*delta is accepted when ||R(u + alpha delta)|| <= (1 - armijo*alpha) ||R(u)||;
-    otherwise alpha is halved (at most ``max_halvings`` times).  Stops when
-    ||R(u_k)|| <= rtol * ||R(u_0)||.  Returns (u, list of residual norms).
+    Each step solves J(u) delta = -R(u) on the assembled sparse Jacobian: ``linear="direct"`` by a
+    sparse direct solve, ``linear="cg"`` by scipy's conjugate gradients with the Jacobi (diagonal)
+    preconditioner to ||J delta + R|| <= cg_rtol ||R|| (the inexact Newton step of the matrix-free
+    solver; the iteration counts go to ``cg_iters``).  A step alpha*delta is accepted when
+    ||R(u + alpha delta)|| <= (1 - armijo*alpha) ||R(u)||; otherwise alpha is halved (at most
+    ``max_halvings`` times).  Stops when ||R(u_k)|| <= rtol * ||R(u_0)||.  Returns (u, list of
+    residual norms).
     """
+    import scipy.sparse as sp
     import scipy.sparse.linalg as spla
+    if linear not in ("direct", "cg"):
+        raise ValueError("linear must be 'direct' or 'cg'")
     u = _f64(u0).copy()
     hist = [] if history is None else history
     r = residual(P, u)
@@ -313,7 +321,17 @@ def newton(P: Problem, u0, rtol: float = 1e-8, max_newton: int = 60, armijo: flo
         if hist[-1] <= rtol * r0:
             break
         J, _ = assemble(P, u)
-        delta = spla.spsolve(J.tocsc(), -r)
+        if linear == "direct":
+            delta = spla.spsolve(J.tocsc(), -r)
+        else:
+            count = [0]
+            Minv = sp.diags(1.0 / J.diagonal())
+            delta, info = spla.cg(J, -r, rtol=cg_rtol, maxiter=20000, M=Minv,
+                                  callback=lambda _x: count.__setitem__(0, count[0] + 1))
+            if info != 0:
+                raise RuntimeError(f"oracle CG did not converge (info {info})")
+            if cg_iters is not None:
+                cg_iters.append(count[0])
         alpha, rn = 1.0, hist[-1]
         for _h in range(max_halvings + 1):
             trial = u + alpha * delta

@@ -95,6 +95,7 @@ _SIGS = {
                              POINTER(c_int)]),
     "fe_launch_count": (c_int, [_CTX, POINTER(c_int64)]),
     "fe_memory_bytes": (c_int, [_CTX, POINTER(c_int64)]),
+    "fe_measure_fp64_peak": (c_int, [c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
     "fe_destroy": (None, [_CTX]),
     "fe_last_error": (c_char_p, [_CTX]),
     "fe_status_string": (c_char_p, [c_int]),
@@ -287,6 +288,14 @@ def fe_memory_bytes(ctx) -> int:
     n = c_int64()
     check(library().fe_memory_bytes(ctx, byref(n)), "fe_memory_bytes", ctx)
     return n.value
+
+
+def fe_measure_fp64_peak(reps: int = 20, stream=None) -> tuple[float, float]:
+    """(best, median) FP64 FMA rate of the current device in TFLOP/s."""
+    best, med = c_double(), c_double()
+    check(library().fe_measure_fp64_peak(reps, byref(best), byref(med), stream_handle(stream)),
+          "fe_measure_fp64_peak")
+    return best.value, med.value
 
 
 def fe_destroy(ctx):

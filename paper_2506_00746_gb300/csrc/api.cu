@@ -1168,9 +1168,12 @@ extern "C" fe_status fe_jacobian_action_noalloc(fe_ctx *c, const void *v, void *
                     need, (unsigned)FE_NOALLOC_SCRATCH_BYTES);
     int dev = -1;
     CK(cudaGetDevice(&dev));
-    if (dev != c->device || dev < 0 || dev >= kMaxDevices)
+    if (dev != c->device)
         return fail(c, FE_ERR_ARG, "fe_jacobian_action_noalloc: current device %d is not the context's (%d)", dev,
                     c->device);
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(c, FE_ERR_ARG, "fe_jacobian_action_noalloc: device index %d beyond the %d the static-scratch "
+                    "address table covers", dev, kMaxDevices);
     void *scratch = nullptr;
     fe_status s = noalloc_scratch_address(c, dev, &scratch);
     if (s != FE_OK) return s;

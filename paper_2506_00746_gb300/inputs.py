@@ -120,11 +120,13 @@ class Workload:
         return self.n ** self.dim
 
 
-# The two fixed single-problem workloads and the 48^3 design workload.
+# The two fixed single-problem workloads, the 48^3 design workload, and a scaled-down 3D problem
+# (16^3, order 2) small enough for a Newton solve by the CPU reference.
 WORKLOADS = {
     "2d_p3_k2_16x16": Workload("2d_p3_k2_16x16", 2, 16, 2),
     "3d_p3_k3_64": Workload("3d_p3_k3_64", 3, 64, 3),
     "3d_design_k2_48": Workload("3d_design_k2_48", 3, 48, 2),
+    "3d_p3_k2_16": Workload("3d_p3_k2_16", 3, 16, 2),
 }
 
 # Order sweep at about 8M DOFs: n chosen so that k*n is about 200.

@@ -16,7 +16,7 @@ HEADER = os.path.join(ROOT, "include", "feod.h")
 def _header_functions() -> set[str]:
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*([a-z_]+)\s*\(", src, flags=re.M))
+    names = set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M))
     return {n for n in names if n.startswith("fe_") or n == "newton_solve"}
 
 

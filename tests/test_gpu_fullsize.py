@@ -88,6 +88,37 @@ def test_config2_sampled_parity():
     op.close()
 
 
+def test_config2_whole_vector_parity():
+    """R(u) and J(u) v at 64^3 order 3 over the whole vector against the oracle's whole-vector
+    R and J v (element by element on the host cores): FP64 and double-float <= 1e-12, FP32 <= 1e-5
+    (against the oracle's J v of the FP32-rounded direction)."""
+    import torch
+    from paper_2506_00746_gb300 import Operator
+    w = I.WORKLOADS["3d_p3_k3_64"]
+    V = I.lattice_vertices(3, w.n, seed=w.mesh_seed)
+    op = Operator(3, w.n, w.order, V, p=w.p)
+    u = I.smooth_field(3, w.n, w.order, seed=w.state_seed)
+    v = I.uniform_vector(op.n_dofs, seed=w.dir_seed)
+    ud, vd = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
+    r = op.residual(ud).cpu().numpy()
+    op.linearize(ud)
+    y64 = op.jacobian_action(vd, precision=64).cpu().numpy()
+    y48 = op.jacobian_action(vd, precision=48).cpu().numpy()
+    v32 = vd.float()
+    y32 = op.jacobian_action(v32, precision=32).double().cpu().numpy()
+    ym32 = op.jacobian_action(vd, precision=-32).cpu().numpy()
+    op.close()
+    P = O.Problem(3, w.n, w.order, V, p=w.p)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(r, O.residual(P, u)) <= 1e-12
+    y_ref = O.jv(P, u, v)
+    assert rel(y64, y_ref) <= 1e-12
+    assert rel(y48, y_ref) <= 1e-12
+    y32_ref = O.jv(P, u, v32.double().cpu().numpy())
+    assert rel(y32, y32_ref) <= 1e-5
+    assert rel(ym32, y32_ref) <= 1e-5
+
+
 def test_design_fullsize_against_oracle():
     """The design case at full size (48^3 hexes, order 2, kappa(rho) = 1e-3 + rho^3, p = 3): the
     oracle evaluates the GPU's Newton solution (its own residual), the GPU's adjoint solution

@@ -1,6 +1,7 @@
 """Error against the FP64 oracle per order on the order-sweep workloads: 3D p-Laplacian p = 3,
 orders 1-6 on jittered hex lattices of about 8M DOFs (k n ~ 200), seeded smooth state and U[-1,1]
 direction.  Per order, over the whole vector:
+  * the FP64 residual against the oracle's R(u) (<= 1e-12 relative);
   * the FP64 and double-float Jacobian actions against the oracle's J(u) v (<= 1e-12 relative);
   * the FP32 action against the oracle's J(u) v at the same FP32-rounded direction (<= 1e-5);
   * the mixed-precision Newton solve (FP32 J v inside an FP64 CG): the oracle evaluates the
@@ -34,6 +35,7 @@ def test_sweep_order_against_oracle(k, n):
     u0 = I.smooth_field(3, n, k, seed=1)
     v = I.uniform_vector(op.n_dofs, seed=2)
     ud, vd = torch.from_numpy(u0).cuda(), torch.from_numpy(v).cuda()
+    r_gpu = op.residual(ud).cpu().numpy()
     op.linearize(ud)
     y64 = op.jacobian_action(vd, precision=64).cpu().numpy()
     y48 = op.jacobian_action(vd, precision=48).cpu().numpy()
@@ -47,13 +49,16 @@ def test_sweep_order_against_oracle(k, n):
     P = O.Problem(3, n, k, V, p=3.0)
     y_ref = O.jv(P, u0, v)
     y32_ref = O.jv(P, u0, v32.double().cpu().numpy())
-    r0 = float(np.linalg.norm(O.residual(P, u0)))
+    r_ref = O.residual(P, u0)
+    r0 = float(np.linalg.norm(r_ref))
     r = float(np.linalg.norm(O.residual(P, uh)))
-    out = {"order": k, "n": n, "n_dofs": int(P.n_dofs), "jv_f64_rel_err": _rel(y64, y_ref),
+    out = {"order": k, "n": n, "n_dofs": int(P.n_dofs), "residual_rel_err": _rel(r_gpu, r_ref),
+           "jv_f64_rel_err": _rel(y64, y_ref),
            "jv_double_float_rel_err": _rel(y48, y_ref), "jv_f32_rel_err": _rel(y32, y32_ref),
            "newton_mixed_steps": rep["newton_iters"], "newton_mixed_cg": rep["cg_iters"],
            "newton_mixed_rel_residual_gpu": rep["rel"], "newton_mixed_rel_residual_oracle": r / r0}
     print(json.dumps(out))
+    assert out["residual_rel_err"] <= 1e-12
     assert out["jv_f64_rel_err"] <= 1e-12
     assert out["jv_double_float_rel_err"] <= 1e-12
     assert out["jv_f32_rel_err"] <= 1e-5
