@@ -9,9 +9,11 @@ double-float action, the FP64 residual, the FP64 action end to end through host 
 full Newton-CG solves (FP64 and mixed precision, to 1e-8 relative residual).
 
 Prints one JSON line.  ``--impl reference`` times the oracle (plain FP64 C on the host cores) on
-a bounded sample of the same workload instead.  Under torchrun every rank runs an independent
-replica on its own GPU (the single-GPU problem does not exchange data); timing is the max over
-ranks and the value sums the work of all ranks.
+a bounded sample of the same workload instead.  Under torchrun (N > 1) the ranks split one problem
+by the subdomain restriction P: each holds a 64^3-element z-slab of a 64 x 64 x 64N lattice (weak
+scaling), and a step is the split FP64 Jacobian action, whose interface planes the neighbours
+exchange (NCCL; ``--backend gloo`` stages them through host memory); timing is the max over
+ranks and the value counts the DOFs of the whole lattice.
 """
 from __future__ import annotations
 
@@ -434,6 +436,128 @@ def run_gpu(args) -> dict | None:
     return out
 
 
+def run_split(args) -> dict | None:
+    """N > 1: one problem split across the ranks by the subdomain restriction P (weak scaling).
+    Every rank holds a z-slab of 64^3 order-3 elements of the lattice 64 x 64 x 64N (each slab
+    the 64^3 workload's jittered cube, shifted to z in [rank, rank + 1], its interface planes
+    unjittered so that neighbours agree); one step is the split FP64 Jacobian action: the local
+    action, then one exchange of the two interface planes with the neighbours."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import dist as D
+    from paper_2506_00746_gb300 import inputs as I
+
+    world, rank, local = dist_env()
+    ndev = torch.cuda.device_count()
+    torch.cuda.set_device(local % ndev)
+    dev = torch.device("cuda", local % ndev)
+    if not dist.is_initialized():
+        if args.backend == "nccl":
+            dist.init_process_group("nccl", device_id=dev)
+        else:
+            dist.init_process_group("gloo")
+    staging = args.backend != "nccl"
+    w = I.WORKLOADS[args.workload]
+    part = D.SlabPartition(w.n, w.order, world, nz=w.n * world)
+    V = I.lattice_vertices(3, w.n, seed=w.mesh_seed + rank).copy()
+    V[:, 2] += rank
+    op = Operator(3, part.elements(rank), w.order, V, p=w.p, eps=w.eps, natural_faces=part.natural_faces(rank))
+    be = D.LibraryBackend(op)
+    comm = D.TorchComm(rank, world, staging=staging)
+    solver = D.SlabSolver(part, rank, be, comm)
+    u0 = torch.from_numpy(I.smooth_field(3, w.n, w.order, seed=w.state_seed)).to(dev)
+    v = torch.from_numpy(I.uniform_vector(op.n_dofs, seed=w.dir_seed + rank)).to(dev)
+    # the shared planes must agree: take the lower neighbour's top plane
+    pl = part.plane
+    lo, _ = comm.exchange(v[:pl].clone(), v[-pl:].clone())
+    if lo is not None:
+        v[:pl] = lo
+    be.linearize(u0)
+    y = be.zeros()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(dev if args.backend == "nccl" else None)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = op.launch_count()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier(dev if args.backend == "nccl" else None)
+        # the exchange synchronises the host (gloo staging): take the larger of device and wall time
+        return max(e0.elapsed_time(e1) / 1e3, wall if staging else 0.0), op.launch_count() - l0
+
+    jv64 = lambda: solver.jv(v, y, 64)
+    clk = ClockSampler(local % ndev).start()
+    t_dev, launches = timed(jv64, args.steps, args.warmup)
+    clocks = clk.stop()
+    t_max = max_over_ranks(t_dev, dev if args.backend == "nccl" else None)
+    value = part.n_dofs * args.steps / t_max / 1e9
+    y32 = be.zeros()
+    jv32 = lambda: solver.jv(v, y32, -32)
+    t32, _ = timed(jv32, args.steps, 3)
+    t32 = max_over_ranks(t32, dev if args.backend == "nccl" else None)
+    # end to end: the rank's slice from pinned host memory, the split action, the result back
+    vh = v.cpu().pin_memory()
+    yh = torch.empty_like(vh).pin_memory()
+    vd = torch.empty_like(v)
+
+    def e2e():
+        vd.copy_(vh, non_blocking=True)
+        solver.jv(vd, y, 64)
+        yh.copy_(y, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    for _ in range(3):
+        e2e()
+    barrier(dev if args.backend == "nccl" else None)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dev if args.backend == "nccl" else None)
+    newton = {}
+    if not args.no_newton:
+        for name, prec in (("mixed", -32), ("fp64", 64)):
+            u = u0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = solver.newton(u, rtol=1e-8, precision=prec, max_newton=args.max_newton)
+            torch.cuda.synchronize()
+            newton[name] = {"time_s": round(max_over_ranks(time.perf_counter() - t0,
+                                                           dev if args.backend == "nccl" else None), 4),
+                            "status": rep["status"], "newton_iters": rep["newton_iters"],
+                            "cg_iters": rep["cg_iters"], "rel_residual": rep["rel"]}
+    op.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (each rank: the seeded jittered 64^3 lattice shifted in z, seeded state and direction)",
+        "config": {"workload": f"{args.workload} per rank: 3D p-Laplacian p=3, 64 x 64 x {64 * world} hex lattice split "
+                               f"in {world} z-slabs, order 3, {part.n_dofs} DOFs; step = one split FP64 J(u) v "
+                               "(local action + one interface exchange)",
+                   "n_dofs": part.n_dofs, "parallelism": f"subdomain split P over {world} ranks ({args.backend})",
+                   "l2": "inputs larger than L2 (FP64 tangent 805 MB per rank)"},
+        "gpu_launches": int(launches), "clocks": clocks,
+        "jv_mixed_gdofs": round(part.n_dofs * args.steps / t32 / 1e9, 4),
+        "e2e": {"value": round(part.n_dofs * args.steps / t_e2e / 1e9, 4), "unit": "GDOF/s",
+                "h2d_bytes_per_step": 8 * op.n_dofs * world, "d2h_bytes_per_step": 8 * op.n_dofs * world},
+        "newton": newton,
+        "exchange_bytes_per_step": 2 * 8 * pl * 2 * (world - 1),
+    }
+
+
 def small_newton_cases(Operator, I) -> dict:
     """Newton solves of the small configurations whose oracle Newton the CPU baseline also times:
     the 2D 16x16 order-2 problem and the 3D 16^3 order-2 problem, FP64 and mixed."""
@@ -781,6 +905,33 @@ def run_jv_small(args) -> dict:
     return out
 
 
+def run_cg_small(args) -> dict:
+    """`reps` Jacobi-preconditioned CG iterations (fe_cg_solve, precision as given) on one 3D p=3
+    instance linearised at the seeded smooth state, with the load vector as right-hand side and an
+    unreachable tolerance (the small case of the CG-kernel captures)."""
+    import torch
+
+    from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import inputs as I
+    from paper_2506_00746_gb300.abi import FeodError
+    torch.cuda.set_device(0)
+    V = I.lattice_vertices(3, args.n, seed=0)
+    op = Operator(3, args.n, args.order, V, p=3.0)
+    u = torch.from_numpy(I.smooth_field(3, args.n, args.order, seed=1)).cuda()
+    op.linearize(u)
+    F = op.load_vector()
+    try:
+        op.cg_solve(F, rtol=1e-30, max_iter=args.reps, precision=args.precision)
+        status = "FE_OK"
+    except FeodError as e:
+        status = str(e).split("(")[1].split(")")[0] if "(" in str(e) else str(e)
+    torch.cuda.synchronize()
+    out = {"suite": "cg", "n": args.n, "order": args.order, "precision": args.precision, "iterations": args.reps,
+           "n_dofs": op.n_dofs, "status": status}
+    op.close()
+    return out
+
+
 def run_batch_subset(args) -> dict:
     """A few batched Jacobian actions on the first `instances` of the 64-instance set (no tuning:
     largest tile edges, largest instances first)."""
@@ -941,7 +1092,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-newton", type=int, default=50)
     ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "element-ad", "jv", "batch-subset",
-                                        "fp64-peak"],
+                                        "fp64-peak", "cg"],
                     default="headline",
                     help="headline (the benchmark line), sweep (orders 1-6), design (adjoint case), batched "
                          "(64 instances in one persistent launch); jv and batch-subset run the small cases "
@@ -953,6 +1104,9 @@ def main(argv=None):
     ap.add_argument("--instances", type=int, default=24)
     ap.add_argument("--orders", default="1,2,3,4,5,6")
     ap.add_argument("--fd-dirs", type=int, default=20)
+    ap.add_argument("--backend", choices=["nccl", "gloo"], default="nccl",
+                    help="N > 1: interface exchange and sums over ranks through NCCL (device buffers) or gloo "
+                         "(host copies; ranks may then share a GPU)")
     ap.add_argument("--save", default=None,
                     help="fp64-peak: also write the result to this JSON file (profiles/fp64_peak.json is the "
                          "committed copy the FP64 rooflines read)")
@@ -961,10 +1115,12 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.suite != "headline" and args.impl == "gpu":
         out = {"sweep": run_sweep, "design": run_design, "batched": run_batched, "element-ad": run_element_ad,
-               "jv": run_jv_small, "fp64-peak": run_fp64_peak,
+               "jv": run_jv_small, "fp64-peak": run_fp64_peak, "cg": run_cg_small,
                "batch-subset": run_batch_subset}[args.suite](args)
+    elif args.impl == "reference":
+        out = run_reference(args)
     else:
-        out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+        out = run_split(args) if dist_env()[0] > 1 else run_gpu(args)
     if out is not None:
         print(json.dumps(out), flush=True)
     import torch.distributed as dist

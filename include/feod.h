@@ -9,13 +9,14 @@
  * matrix-free Newton-CG solve and the adjoint design gradient (the adjoint loads of the
  * design-sensitivity discussion that follows Eq. 3).
  *
- * Discretisation: structured lattice of n^dim elements on the unit box (dim = 2 or 3) with
+ * Discretisation: structured lattice of n[0] x n[1] (x n[2]) elements (dim = 2 or 3) with
  * caller-given (jittered) vertices and a multilinear geometry map per element; continuous
  * Lagrange basis of order k = 1..6 on Gauss-Lobatto-Legendre nodes; (k+1)^dim Gauss-Legendre
- * points per element.  DOFs form the lattice (k n + 1)^dim, numbered lexicographically with x
- * fastest; elements are numbered ex + n (ey + n ez).  Essential (Dirichlet) DOFs are all DOFs on
- * the boundary of the box.  On one GPU the subdomain restriction P is the identity plus this
- * Dirichlet elimination:
+ * points per element.  DOFs form the lattice (k n[0] + 1) x (k n[1] + 1) (x (k n[2] + 1)),
+ * numbered lexicographically with x fastest; elements are numbered ex + n[0] (ey + n[1] ez).
+ * Essential (Dirichlet) DOFs are the DOFs on the boundary of the lattice's box, except on faces
+ * marked natural (subdomain interfaces).  On one GPU the subdomain restriction P is the identity
+ * plus this Dirichlet elimination:
  *   - R(u) = A(u) - F with R_i = 0 on essential DOFs (u carries the boundary values);
  *   - J(u) v treats essential entries of v as zero and returns y_i = v_i on essential DOFs,
  *     so J is symmetric positive (semi)definite.
@@ -56,12 +57,18 @@ typedef enum {
                                   fe_linearize)                                               */
 } fe_status;
 
-/* Structured lattice mesh.  `vertices` is a HOST array [(n+1)^dim][dim], lexicographic with x
- * fastest; it is copied during fe_setup. */
+/* Structured lattice mesh of n[0] x n[1] (x n[2]) elements.  `vertices` is a HOST array
+ * [(n[0]+1)(n[1]+1)(n[2]+1)][dim] (the last factor absent in 2D), lexicographic with x fastest; it
+ * is copied during fe_setup.  natural_faces: the faces of the lattice's box whose DOFs are NOT
+ * essential -- the boundary between this subdomain and its neighbours when the problem is split
+ * by the subdomain restriction P (Fig. 1), where the neighbours' partial sums complete the
+ * operator; bits 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+ (0 = every boundary DOF essential, the
+ * single-domain problem). */
 typedef struct {
     int dim;                   /* 2 or 3                                                      */
-    int n;                     /* elements per direction, >= 1                                */
+    int n[3];                  /* elements per direction x, y, z, each >= 1 (n[2] unused in 2D) */
     const double *vertices;
+    int natural_faces;         /* mask of non-essential box faces (see above)                 */
 } fe_mesh;
 
 /* The pointwise law and the load.  kappa_rho(rho) = kappa_eps + rho^kappa_q multiplies the flux
@@ -71,7 +78,7 @@ typedef struct {
     double eps;                /* regularisation of |grad u|^2 (0 = the plain p-Laplacian)     */
     int f_kind;                /* 0: f = f_const; 1: manufactured source of u* = exp(x+y/2+z/3) */
     double f_const;
-    const double *rho;         /* host, [n^dim] or NULL                                       */
+    const double *rho;         /* host, one value per element [N_e] or NULL                  */
     double kappa_eps;
     double kappa_q;
 } fe_problem;
@@ -186,7 +193,7 @@ fe_status fe_load_vector(fe_ctx *ctx, double *F, void *stream);
 /* fe_node_coords: physical coordinates of every DOF, device double[N_L][dim]. */
 fe_status fe_node_coords(fe_ctx *ctx, double *xyz, void *stream);
 
-/* fe_set_design: replace the per-element design field rho (device double[n^dim], copied on the
+/* fe_set_design: replace the per-element design field rho (device double[N_e], copied on the
  * stream).  Invalidates the cached linearisation. */
 fe_status fe_set_design(fe_ctx *ctx, const double *rho, void *stream);
 
@@ -195,7 +202,7 @@ fe_status fe_set_design(fe_ctx *ctx, const double *rho, void *stream);
  * obtained by seeding a dual number on rho at each quadrature point (AD local to the quadrature
  * point; no scatter, element-local reduction).  For the compliance c = F^T u with R(u; rho) = 0,
  * dc/drho = -grad_rho evaluated at the adjoint solution J lambda = F.  Needs a design field.
- * u, lambda: device double[N_L]; grad_rho: device double[n^dim] (element order ex fastest). */
+ * u, lambda: device double[N_L]; grad_rho: device double[N_e] (element order ex fastest). */
 fe_status fe_adjoint_vjp(fe_ctx *ctx, const double *u, const double *lambda, double *grad_rho,
                          void *stream);
 
@@ -280,6 +287,34 @@ fe_status newton_solve(fe_ctx *ctx, double *u_inout, const fe_newton_opts *opts,
  * Synchronous.  iters may be NULL. */
 fe_status fe_cg_solve(fe_ctx *ctx, const double *b, double *x, double rtol, int max_iter,
                       int precision, int *iters, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Vector operations on device vectors of a context's length N_L, FP64, stream-ordered: the CG's
+ * building blocks, exposed for solvers that run outside the library -- in particular the
+ * subdomain-split solve, where the subdomain restriction P (Fig. 1) puts one exchange of
+ * interface values after each local operator application and a sum over ranks after each local
+ * inner product.  Calls on one context must not overlap on the GPU (fe_dot's reduction scratch
+ * belongs to the context).
+ * --------------------------------------------------------------------------------------------- */
+/* fe_dot: *out (a DEVICE double) = sum_{begin <= i < end} a_i b_i, summed in a fixed order (the
+ * same range gives the same bits on the same GPU model).  FE_ERR_ARG for a range outside [0, N_L]. */
+fe_status fe_dot(fe_ctx *ctx, const double *a, const double *b, int64_t begin, int64_t end, double *out,
+                 void *stream);
+/* fe_axpby: y = alpha x + beta y (with beta == 0, y is only written). */
+fe_status fe_axpby(fe_ctx *ctx, double alpha, const double *x, double beta, double *y, void *stream);
+/* fe_pointwise_mul: z_i = d_i r_i (z may alias r; the Jacobi scaling of a residual). */
+fe_status fe_pointwise_mul(fe_ctx *ctx, const double *d, const double *r, double *z, void *stream);
+/* fe_reciprocal: y_i = 1 / x_i (y may alias x). */
+fe_status fe_reciprocal(fe_ctx *ctx, const double *x, double *y, void *stream);
+/* Faces of the DOF lattice: face 2a + s is the plane where coordinate a (0 x, 1 y, 2 z) is 0
+ * (s = 0) or its last value (s = 1).  fe_face_size: number of DOFs of the face.  fe_face_add:
+ * y_g += buf_i for the face's i-th DOF g (DOFs in lexicographic order of the two other axes, lower
+ * axis fastest), on non-essential DOFs only (essential ones keep their value) -- P^T across an
+ * interface: the neighbour's partial sums of the shared DOFs added to this subdomain's.  For
+ * face 4 (z = 0) and 5 (z = last) of a 3D lattice the face's DOFs are the contiguous first and
+ * last (k n[0] + 1)(k n[1] + 1) entries of a vector, so buf can be a neighbour's slice as is. */
+fe_status fe_face_size(const fe_ctx *ctx, int face, int64_t *size);
+fe_status fe_face_add(fe_ctx *ctx, int face, double *y, const double *buf, void *stream);
 
 /* Profiling: when enabled, every kernel launch is bracketed by CUDA events on its stream.
  * fe_prof_read synchronises, then returns for kernel name index i (0 <= i < *count) its name,

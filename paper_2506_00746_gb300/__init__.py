@@ -25,14 +25,18 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
 class Operator:
     """One problem instance on one GPU (a ``fe_ctx``).
 
-    ``vertices``: host array [(n+1)^dim, dim] (x fastest).  ``rho``: optional per-element design
+    ``n``: elements per direction, an int (a cube lattice) or a sequence of ``dim`` counts.
+    ``vertices``: host array [prod(n_d + 1), dim] (x fastest).  ``rho``: optional per-element design
     field (host array, element order ex fastest), which makes the flux kappa_rho(rho_e) times the
-    p-Laplacian flux with kappa_rho = kappa_eps + rho^kappa_q.
+    p-Laplacian flux with kappa_rho = kappa_eps + rho^kappa_q.  ``natural_faces``: mask of the box
+    faces whose DOFs are not essential (bits x-, x+, y-, y+, z-, z+), the interfaces of a
+    subdomain.
     """
 
-    def __init__(self, dim: int, n: int, order: int, vertices, p: float = 3.0, eps: float = 0.0,
+    def __init__(self, dim: int, n, order: int, vertices, p: float = 3.0, eps: float = 0.0,
                  f_kind: int = 0, f_const: float = 1.0, rho=None, kappa_eps: float = 1e-3,
-                 kappa_q: float = 3.0, q1d: int = 0, tile: int = 0, tile_kernel: bool = True):
+                 kappa_q: float = 3.0, q1d: int = 0, tile: int = 0, tile_kernel: bool = True,
+                 natural_faces: int = 0):
         import ctypes
 
         import torch
@@ -40,7 +44,7 @@ class Operator:
             raise RuntimeError("Operator needs a CUDA device: the library has no CPU path")
         self._vert = np.ascontiguousarray(vertices, dtype=np.float64)
         self._rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
-        mesh = abi.fe_mesh(dim, n, self._vert.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        mesh = abi.make_mesh(dim, n, self._vert.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), natural_faces)
         prob = abi.fe_problem(p, eps, f_kind, f_const,
                               None if self._rho is None else self._rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                               kappa_eps, kappa_q)
@@ -223,7 +227,7 @@ class Batch:
         items = (abi.fe_batch_item * self.count)()
         for i, d in enumerate(instances):
             vert = np.ascontiguousarray(d["vertices"], dtype=np.float64)
-            mesh = abi.fe_mesh(3, int(d["n"]), vert.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+            mesh = abi.make_mesh(3, int(d["n"]), vert.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
             prob = abi.fe_problem(float(d.get("p", 3.0)), float(d.get("eps", 0.0)), int(d.get("f_kind", 0)),
                                   float(d.get("f_const", 1.0)), None, 1e-3, 3.0)
             self._keep += [vert, mesh, prob]

@@ -11,6 +11,8 @@ import ctypes
 import os
 from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int64, c_void_p
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libfeod.so")
 
@@ -30,7 +32,22 @@ FE_OK = 0
 
 
 class fe_mesh(ctypes.Structure):
-    _fields_ = [("dim", c_int), ("n", c_int), ("vertices", POINTER(c_double))]
+    _fields_ = [("dim", c_int), ("n", c_int * 3), ("vertices", POINTER(c_double)), ("natural_faces", c_int)]
+
+
+def make_mesh(dim: int, n, vertices_ptr, natural_faces: int = 0) -> fe_mesh:
+    """fe_mesh for a lattice of n elements per direction (an int: the same in every direction, or
+    a sequence of dim counts)."""
+    nn = [int(n)] * dim if isinstance(n, (int, np.integer)) else [int(x) for x in n]
+    if len(nn) != dim:
+        raise ValueError(f"n needs {dim} element counts")
+    m = fe_mesh()
+    m.dim = dim
+    for d in range(3):
+        m.n[d] = nn[d] if d < dim else 1
+    m.vertices = vertices_ptr
+    m.natural_faces = int(natural_faces)
+    return m
 
 
 class fe_problem(ctypes.Structure):
@@ -96,6 +113,12 @@ _SIGS = {
     "fe_launch_count": (c_int, [_CTX, POINTER(c_int64)]),
     "fe_memory_bytes": (c_int, [_CTX, POINTER(c_int64)]),
     "fe_measure_fp64_peak": (c_int, [c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "fe_dot": (c_int, [_CTX, c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
+    "fe_axpby": (c_int, [_CTX, c_double, c_void_p, c_double, c_void_p, c_void_p]),
+    "fe_pointwise_mul": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fe_reciprocal": (c_int, [_CTX, c_void_p, c_void_p, c_void_p]),
+    "fe_face_size": (c_int, [_CTX, c_int, POINTER(c_int64)]),
+    "fe_face_add": (c_int, [_CTX, c_int, c_void_p, c_void_p, c_void_p]),
     "fe_destroy": (None, [_CTX]),
     "fe_last_error": (c_char_p, [_CTX]),
     "fe_status_string": (c_char_p, [c_int]),
@@ -296,6 +319,33 @@ def fe_measure_fp64_peak(reps: int = 20, stream=None) -> tuple[float, float]:
     check(library().fe_measure_fp64_peak(reps, byref(best), byref(med), stream_handle(stream)),
           "fe_measure_fp64_peak")
     return best.value, med.value
+
+
+def fe_dot(ctx, a, b, begin: int, end: int, out, stream=None):
+    """out (a device double tensor of one entry) = a[begin:end] . b[begin:end]."""
+    check(library().fe_dot(ctx, ptr(a), ptr(b), begin, end, ptr(out), stream_handle(stream)), "fe_dot", ctx)
+
+
+def fe_axpby(ctx, alpha: float, x, beta: float, y, stream=None):
+    check(library().fe_axpby(ctx, alpha, ptr(x), beta, ptr(y), stream_handle(stream)), "fe_axpby", ctx)
+
+
+def fe_pointwise_mul(ctx, d, r, z, stream=None):
+    check(library().fe_pointwise_mul(ctx, ptr(d), ptr(r), ptr(z), stream_handle(stream)), "fe_pointwise_mul", ctx)
+
+
+def fe_reciprocal(ctx, x, y, stream=None):
+    check(library().fe_reciprocal(ctx, ptr(x), ptr(y), stream_handle(stream)), "fe_reciprocal", ctx)
+
+
+def fe_face_size(ctx, face: int) -> int:
+    n = c_int64()
+    check(library().fe_face_size(ctx, face, byref(n)), "fe_face_size", ctx)
+    return n.value
+
+
+def fe_face_add(ctx, face: int, y, buf, stream=None):
+    check(library().fe_face_add(ctx, face, ptr(y), ptr(buf), stream_handle(stream)), "fe_face_add", ctx)
 
 
 def fe_destroy(ctx):

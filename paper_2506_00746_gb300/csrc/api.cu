@@ -445,8 +445,11 @@ extern "C" fe_status fe_setup(const fe_mesh *mesh, int order, int q1d, const fe_
 static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_problem *prob,
                             const fe_setup_opts *opts)
 {
-    const int dim = mesh->dim, n = mesh->n, k = order;
-    c->dim = dim; c->n = n; c->k = k; c->d1 = k + 1; c->q1 = k + 1;
+    const int dim = mesh->dim, k = order;
+    c->dim = dim; c->k = k; c->d1 = k + 1; c->q1 = k + 1;
+    for (int d = 0; d < 3; ++d) c->n[d] = d < dim ? mesh->n[d] : 1;
+    c->natural = mesh->natural_faces & (dim == 3 ? 63 : 15);
+    const int *n = c->n;
     c->NQ = (int)ipow64(c->q1, dim);
     c->NS = dim == 3 ? 6 : 3;
     c->NG = c->NS + 2;
@@ -454,10 +457,16 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     c->kappa_eps = prob->kappa_eps; c->kappa_q = prob->kappa_q;
     c->has_rho = prob->rho != nullptr;
     c->law = (prob->p == 2.0) ? LAW_P2 : (prob->p == 3.0) ? LAW_P3 : (prob->p == 4.0) ? LAW_P4 : LAW_GENERIC;
-    const int64_t m = (int64_t)k * n + 1;
-    c->nl = ipow64(m, dim);
-    c->nfree = ipow64(m - 2 > 0 ? m - 2 : 0, dim);
-    c->ne = ipow64(n, dim);
+    // DOF lattice (k n_d + 1) per direction; a DOF is essential when it lies on a box face that
+    // is not natural
+    int64_t m[3] = { 1, 1, 1 }, mfree[3] = { 1, 1, 1 };
+    for (int d = 0; d < dim; ++d) {
+        m[d] = (int64_t)k * n[d] + 1;
+        mfree[d] = m[d] - ((c->natural >> (2 * d)) & 1 ? 0 : 1) - ((c->natural >> (2 * d + 1)) & 1 ? 0 : 1);
+    }
+    c->nl = m[0] * m[1] * m[2];
+    c->nfree = mfree[0] * mfree[1] * mfree[2];
+    c->ne = (int64_t)n[0] * n[1] * n[2];
     if (c->nl > MAX_DOFS) return fail(c, FE_ERR_UNSUPPORTED, "%lld DOFs exceed the 2^30-1 limit", (long long)c->nl);
 
     CK(cudaGetDevice(&c->device));
@@ -473,7 +482,8 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     // tile size
     int T = (opts && opts->tile > 0) ? opts->tile : default_tile(dim, k);
     if (T > max_tile(dim, k)) T = max_tile(dim, k);
-    if (T > n) T = n;
+    for (int d = 0; d < dim; ++d)
+        if (T > n[d]) T = n[d];
     const int team = dim == 3 ? c->d1 * c->d1 : c->d1;
     for (;;) {
         const int NE = (int)ipow64(T, dim);
@@ -484,8 +494,8 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     }
     c->T = T;
     c->NE = (int)ipow64(T, dim);
-    c->nt = (n + T - 1) / T;
-    c->ntiles = ipow64(c->nt, dim);
+    for (int d = 0; d < 3; ++d) c->nt[d] = d < dim ? (n[d] + T - 1) / T : 1;
+    c->ntiles = (int64_t)c->nt[0] * c->nt[1] * c->nt[2];
     c->nepad = c->ntiles * c->NE;
     c->SE = k * T + 1;
     c->S = (int)ipow64(c->SE, dim);
@@ -531,20 +541,21 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     std::vector<uint64_t> halo_pairs;   // (g << 32) | (t*S + s)
     for (int64_t t = 0; t < c->ntiles; ++t) {
         int64_t tc[3] = { 0, 0, 0 }, r = t;
-        for (int d = 0; d < dim; ++d) { tc[d] = r % c->nt; r /= c->nt; }
+        for (int d = 0; d < dim; ++d) { tc[d] = r % c->nt[d]; r /= c->nt[d]; }
         for (int s = 0; s < c->S; ++s) {
             int sc[3] = { s % c->SE, (s / c->SE) % c->SE, dim == 3 ? s / (c->SE * c->SE) : 0 };
             bool valid = true, ess = false, halo = false;
             int64_t gl[3] = { 0, 0, 0 };
             for (int d = 0; d < dim; ++d) {
                 gl[d] = (int64_t)k * T * tc[d] + sc[d];
-                if (gl[d] > (int64_t)k * n) valid = false;
-                if (gl[d] == 0 || gl[d] == (int64_t)k * n) ess = true;
-                if (sc[d] == k * T && tc[d] < c->nt - 1) halo = true;
+                if (gl[d] > (int64_t)k * n[d]) valid = false;
+                if (gl[d] == 0 && !((c->natural >> (2 * d)) & 1)) ess = true;
+                if (gl[d] == (int64_t)k * n[d] && !((c->natural >> (2 * d + 1)) & 1)) ess = true;
+                if (sc[d] == k * T && tc[d] < c->nt[d] - 1) halo = true;
             }
             uint32_t code = SLOT_INVALID;
             if (valid) {
-                const int64_t g = gl[0] + m * (gl[1] + (dim == 3 ? m * gl[2] : 0));
+                const int64_t g = gl[0] + m[0] * (gl[1] + (dim == 3 ? m[1] * gl[2] : 0));
                 code = (uint32_t)g | (ess ? SLOT_ESS : 0u) | (halo ? SLOT_HALO : 0u);
                 if (halo && !ess) halo_pairs.push_back(((uint64_t)g << 32) | (uint64_t)(t * c->Spad + s));
             }
@@ -594,11 +605,12 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
         c->b32.Dc[i] = (float)cder[i];
         c->bdf.Dc[i] = dfloat(cder[i]);
     }
-    c->gp.dim = dim; c->gp.d1 = c->d1; c->gp.q1 = c->q1; c->gp.n = n; c->gp.T = T; c->gp.nt = c->nt;
+    c->gp.dim = dim; c->gp.d1 = c->d1; c->gp.q1 = c->q1; c->gp.T = T;
+    for (int d = 0; d < 3; ++d) { c->gp.n[d] = n[d]; c->gp.nt[d] = c->nt[d]; }
     c->gp.nepad = c->nepad; c->gp.f_kind = prob->f_kind; c->gp.f_const = prob->f_const; c->gp.p = prob->p;
 
     // --- device data ---
-    const int64_t nvert = ipow64(n + 1, dim);
+    const int64_t nvert = (int64_t)(n[0] + 1) * (n[1] + 1) * (dim == 3 ? n[2] + 1 : 1);
     CK(dalloc(c, &c->d_gt_off, gt_off.size()));
     CK(dalloc(c, &c->d_gt_src, gt_src.size()));
     CK(cudaMemcpy(c->d_gt_off, gt_off.data(), gt_off.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
@@ -644,7 +656,8 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     if (herr) return fail(c, FE_ERR_MESH, "det J <= 0 at a quadrature point (inverted or degenerate element)");
 
     // --- kernel parameter blocks ---
-    c->op.n = n; c->op.T = T; c->op.nt = c->nt; c->op.S = c->S; c->op.SE = c->SE; c->op.law = c->law;
+    for (int d = 0; d < 3; ++d) { c->op.n[d] = n[d]; c->op.nt[d] = c->nt[d]; }
+    c->op.T = T; c->op.S = c->S; c->op.SE = c->SE; c->op.law = c->law;
     c->op.ntiles = c->ntiles; c->op.slot = c->d_slot; c->op.geo = c->d_geo;
     c->op.Spad = c->Spad; c->op.tqs32 = c->tqs32; c->op.tqs64 = c->tqs64;
     c->op.gt_off = c->d_gt_off; c->op.gt_src = c->d_gt_src; c->op.err = c->d_err;
@@ -666,8 +679,13 @@ extern "C" fe_status fe_setup_ex(const fe_mesh *mesh, int order, int q1d, const 
     if (!out) return FE_ERR_ARG;
     *out = nullptr;
     g_setup_error.clear();
-    if (!mesh || !prob || !mesh->vertices || (mesh->dim != 2 && mesh->dim != 3) || mesh->n < 1) {
+    if (!mesh || !prob || !mesh->vertices || (mesh->dim != 2 && mesh->dim != 3) || mesh->n[0] < 1 ||
+        mesh->n[1] < 1 || (mesh->dim == 3 && mesh->n[2] < 1)) {
         g_setup_error = "invalid mesh or problem";
+        return FE_ERR_ARG;
+    }
+    if (mesh->natural_faces < 0 || mesh->natural_faces > (mesh->dim == 3 ? 63 : 15)) {
+        g_setup_error = "natural_faces must be a mask of the box faces (bits 0-5 in 3D, 0-3 in 2D)";
         return FE_ERR_ARG;
     }
     if (order < 1 || order > MAX_ORDER) { g_setup_error = "order must be 1..6"; return FE_ERR_UNSUPPORTED; }
@@ -1121,6 +1139,97 @@ extern "C" fe_status fe_launch_count(const fe_ctx *c, int64_t *launches)
 {
     if (!c || !launches) return FE_ERR_ARG;
     *launches = c->launches;
+    return FE_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// vector operations (the CG's building blocks, for solvers outside the library)
+// ------------------------------------------------------------------------------------------------
+extern "C" fe_status fe_dot(fe_ctx *c, const double *a, const double *b, int64_t begin, int64_t end, double *out,
+                            void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!a || !b || !out || begin < 0 || end > c->nl || begin > end)
+        return fail(c, FE_ERR_ARG, "fe_dot: null vectors or range outside [0, N_L]");
+    fe_status s = ensure_work(c);
+    if (s != FE_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    CgState *ds = cg_state(c) + 1;
+    {
+        LaunchScope ls(c, "dot", st);
+        k_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a + begin, b + begin, end - begin, c->w_partial + 2 * RED_BLOCKS,
+                                                  &ds->counter, out);
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_axpby(fe_ctx *c, double alpha, const double *x, double beta, double *y, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!x || !y) return fail(c, FE_ERR_ARG, "fe_axpby: null vectors");
+    cudaStream_t st = as_stream(stream);
+    {
+        LaunchScope ls(c, "axpby", st);
+        k_axpby<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(alpha, x, beta, y, c->nl);
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_pointwise_mul(fe_ctx *c, const double *d, const double *r, double *z, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!d || !r || !z) return fail(c, FE_ERR_ARG, "fe_pointwise_mul: null vectors");
+    cudaStream_t st = as_stream(stream);
+    {
+        LaunchScope ls(c, "pointwise_mul", st);
+        k_mul<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(d, r, z, c->nl);
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_reciprocal(fe_ctx *c, const double *x, double *y, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!x || !y) return fail(c, FE_ERR_ARG, "fe_reciprocal: null vectors");
+    cudaStream_t st = as_stream(stream);
+    {
+        LaunchScope ls(c, "reciprocal", st);
+        k_recip<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(x, y, c->nl);
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_face_size(const fe_ctx *c, int face, int64_t *size)
+{
+    if (!c || !size || face < 0 || face >= 2 * c->dim) return FE_ERR_ARG;
+    int64_t m[3] = { 1, 1, 1 };
+    for (int d = 0; d < c->dim; ++d) m[d] = (int64_t)c->k * c->n[d] + 1;
+    const int ax = face / 2;
+    *size = m[0] * m[1] * m[2] / m[ax];
+    return FE_OK;
+}
+
+extern "C" fe_status fe_face_add(fe_ctx *c, int face, double *y, const double *buf, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!y || !buf || face < 0 || face >= 2 * c->dim) return fail(c, FE_ERR_ARG, "fe_face_add: bad face or null vectors");
+    FaceParams F{};
+    F.dim = c->dim;
+    F.face = face;
+    F.natural = c->natural;
+    for (int d = 0; d < 3; ++d) F.m[d] = d < c->dim ? (int64_t)c->k * c->n[d] + 1 : 1;
+    int64_t size = 0;
+    fe_face_size(c, face, &size);
+    cudaStream_t st = as_stream(stream);
+    {
+        LaunchScope ls(c, "face_add", st);
+        k_face_add<<<(unsigned)((size + 255) / 256), 256, 0, st>>>(F, y, buf);
+    }
+    CKLAUNCH();
     return FE_OK;
 }
 

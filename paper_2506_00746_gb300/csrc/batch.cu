@@ -972,6 +972,11 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
             g_batch_setup_error = "batched instances are 3D of order 1..4";
             return items[i].order > BATCH_MAX_ORDER ? FE_ERR_UNSUPPORTED : FE_ERR_ARG;
         }
+        const int *nn = items[i].mesh->n;
+        if (nn[0] != nn[1] || nn[0] != nn[2] || items[i].mesh->natural_faces != 0) {
+            g_batch_setup_error = "batched instances are cube lattices (n[0] = n[1] = n[2]) with every face essential";
+            return FE_ERR_UNSUPPORTED;
+        }
     }
     fe_batch *b = new (std::nothrow) fe_batch();
     if (!b) return FE_ERR_OOM;
@@ -995,7 +1000,7 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
     for (int k = 1; k <= BATCH_MAX_ORDER && s == FE_OK; ++k) {
         int rep = -1;     // representative: the largest instance of order k
         for (int i = 0; i < count; ++i)
-            if (b->order[i] == k && (rep < 0 || items[i].mesh->n > items[rep].mesh->n)) rep = i;
+            if (b->order[i] == k && (rep < 0 || items[i].mesh->n[0] > items[rep].mesh->n[0])) rep = i;
         if (rep < 0) continue;
         const int tmax = bv_max_tile(k), tmin = bv_min_tile(k);
         if (o.tile[k - 1] > 0) {
@@ -1004,7 +1009,7 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
             continue;
         }
         char key[256];
-        std::snprintf(key, sizeof key, "%s|order%d|n%d|tile", gpu.c_str(), k, items[rep].mesh->n);
+        std::snprintf(key, sizeof key, "%s|order%d|n%d|tile", gpu.c_str(), k, items[rep].mesh->n[0]);
         double cached = 0.0;
         if (!o.retune && have_cache && cache.get(key, &cached) && (cached == tmax || cached == tmin)) {
             chosen[k] = (int)cached;
@@ -1014,7 +1019,7 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
         // measure the representative instance alone with both tile edges
         double best_ms = 1e300;
         for (int T : { tmax, tmin }) {
-            if (T < 1 || T > items[rep].mesh->n) continue;
+            if (T < 1 || T > items[rep].mesh->n[0]) continue;
             fe_batch one;
             one.count = 1;
             one.device = b->device;
@@ -1041,10 +1046,10 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
         if (s == FE_OK) { cache.set(key, chosen[k]); cache_dirty = true; }
     }
     for (int i = 0; i < count && s == FE_OK; ++i) {
-        b->tile[i] = fit_tile(b->order[i], chosen[b->order[i]], items[i].mesh->n);
+        b->tile[i] = fit_tile(b->order[i], chosen[b->order[i]], items[i].mesh->n[0]);
         if (b->tile[i] < 1) {
             s = bfail(b, FE_ERR_UNSUPPORTED, "instance %d: n = %d is below every tile edge compiled for order %d", i,
-                      items[i].mesh->n, b->order[i]);
+                      items[i].mesh->n[0], b->order[i]);
             break;
         }
         b->variant[i] = bv_of(b->order[i], b->tile[i]);
@@ -1058,7 +1063,7 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
         char key[256];
         uint64_t sig = 1469598103934665603ull;       // FNV-1a over (order, n, tile) of every instance
         for (int i = 0; i < count; ++i)
-            for (int x : { b->order[i], items[i].mesh->n, b->tile[i] }) { sig ^= (uint64_t)x; sig *= 1099511628211ull; }
+            for (int x : { b->order[i], items[i].mesh->n[0], b->tile[i] }) { sig ^= (uint64_t)x; sig *= 1099511628211ull; }
         std::snprintf(key, sizeof key, "%s|batch%016llx", gpu.c_str(), (unsigned long long)sig);
         double cached = 0.0;
         const int per_sm_max = b->grid / std::max(b->num_sms, 1);

@@ -71,12 +71,12 @@ __global__ void __launch_bounds__(ELEM_THREADS)
         gt[(q * 3 + 1) * NL + l] = bx * Bs.G[qy * D1 + b] * bz;
         gt[(q * 3 + 2) * NL + l] = bx * by * Bs.G[qz * D1 + c];
     }
-    const int n = P.n, T = P.T, nt = P.nt;
-    const int64_t m = (int64_t)K1 * n + 1;
+    const int nx = P.n[0], ny = P.n[1], T = P.T;
+    const int64_t mx = (int64_t)K1 * nx + 1, my = (int64_t)K1 * ny + 1;
     for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
         const int64_t e = e0 + i;
-        const int ex = (int)(e % n), ey = (int)((e / n) % n), ez = (int)(e / ((int64_t)n * n));
-        const int64_t t = (ex / T) + (int64_t)nt * ((ey / T) + (int64_t)nt * (ez / T));
+        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+        const int64_t t = (ex / T) + (int64_t)P.nt[0] * ((ey / T) + (int64_t)P.nt[1] * (ez / T));
         const int el = (ex % T) + T * ((ey % T) + T * (ez % T));
         const int64_t eint = t * (int64_t)(T * T * T) + el;
         const double *ge = P.geo + eint * (int64_t)(8 * NQ);
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(ELEM_THREADS)
         __syncthreads();                                    // previous element done with ue, gm, wk
         for (int l = tid; l < NL; l += ELEM_THREADS) {
             const int a = l % D1, b = (l / D1) % D1, c = l / (D1 * D1);
-            ue[l] = u[(K1 * ex + a) + m * ((K1 * ey + b) + m * (int64_t)(K1 * ez + c))];
+            ue[l] = u[(K1 * ex + a) + mx * ((K1 * ey + b) + my * (int64_t)(K1 * ez + c))];
         }
         for (int q = tid; q < NQ; q += ELEM_THREADS)
             for (int c = 0; c < 7; ++c) gm[q * 7 + c] = ge[c * NQ + q];

@@ -190,8 +190,8 @@ __device__ __forceinline__ TileInfo tile_info(const OpParams &P, int64_t t)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         if (d < DIM) {
-            ti.T1[d] = (int)(r % P.nt); r /= P.nt;
-            int rem = P.n - ti.T1[d] * P.T;
+            ti.T1[d] = (int)(r % P.nt[d]); r /= P.nt[d];
+            int rem = P.n[d] - ti.T1[d] * P.T;
             ti.nv[d] = rem < P.T ? rem : P.T;
         } else {
             ti.T1[d] = 0; ti.nv[d] = 1;
@@ -220,7 +220,7 @@ __device__ __forceinline__ int64_t elem_public(const OpParams &P, const TileInfo
 {
     int64_t ex = (int64_t)ti.T1[0] * P.T + c[0], ey = (int64_t)ti.T1[1] * P.T + c[1];
     int64_t ez = (int64_t)ti.T1[2] * P.T + c[2];
-    return ex + P.n * (ey + (DIM == 3 ? P.n * ez : 0));
+    return ex + P.n[0] * (ey + (DIM == 3 ? P.n[1] * ez : 0));
 }
 
 // G (and P for a Jacobian input): gather the tile's DOF block into shared memory.

@@ -64,9 +64,9 @@ enum LawKind : int { LAW_GENERIC = 0, LAW_P2 = 1, LAW_P3 = 2, LAW_P4 = 3 };
 
 // Everything the element kernels need about the mesh, tiling and law.
 struct OpParams {
-    int n;            // elements per direction
+    int n[3];         // elements per direction (x, y, z; 1 beyond dim)
     int T;            // tile edge in elements
-    int nt;           // tiles per direction
+    int nt[3];        // tiles per direction
     int S;            // slots per tile = (k T + 1)^dim
     int SE;           // slots per tile edge = k T + 1
     int Spad;         // per-tile stride of slot codes and halo entries (S rounded up to 4)
@@ -98,7 +98,8 @@ struct FixParams {
 
 // Geometry setup parameters.
 struct GeomParams {
-    int dim, d1, q1, n, T, nt;
+    int dim, d1, q1, T;
+    int n[3], nt[3];               // elements and tiles per direction (1 beyond dim)
     int64_t nepad;
     double xq[MAXQ], wq[MAXQ];     // Gauss points / weights on [0,1]
     double xn[MAXQ];               // GLL nodes on [0,1]
@@ -141,8 +142,11 @@ const OpTable *find_ops(int dim, int d1);
 
 // The context.  Owns all device memory it allocates.
 struct fe_ctx {
-    int dim = 0, n = 0, k = 0, d1 = 0, q1 = 0;
-    int T = 0, nt = 0, S = 0, SE = 0, NE = 0;   // tiling
+    int dim = 0, k = 0, d1 = 0, q1 = 0;
+    int n[3] = { 1, 1, 1 };                     // elements per direction (1 beyond dim)
+    int natural = 0;                            // mask of box faces whose DOFs are not essential
+    int T = 0, S = 0, SE = 0, NE = 0;           // tiling
+    int nt[3] = { 1, 1, 1 };                    // tiles per direction
     int Spad = 0;                               // per-tile slot stride
     int64_t tqs32 = 0, tqs64 = 0;               // per-tile tangent strides (elements)
     uint16_t *d_gt_off = nullptr, *d_gt_src = nullptr;   // in-tile G^T table

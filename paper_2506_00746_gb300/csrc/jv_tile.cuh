@@ -50,17 +50,41 @@ struct TileShape {
     static constexpr int NSZ = (TT - 1) * SE * SE;
 };
 
-// Shared memory of the generic (collocated) tile kernel: mbarrier, tangent block, slot codes, halo
-// positions, gathered DOF block, the z/y^T array A, the y/x^T array C, the point arrays U, FX, FY,
-// FZ and the seam planes.
+// Shared memory of the generic (collocated) tile kernel, in bytes from the dynamic base.  Arrays
+// whose live ranges (between the kernel's barriers) do not overlap share storage:
+//   Vs, the gathered DOF block (written by the prologue, read by z) lies inside C (first written
+//       by y);
+//   U, the values at the points (written by x1, read by x2) lies inside A (read by y, next
+//       written by yT);
+//   the seam planes SX, SY, SZ (written from x3 on) lie inside the tangent block Tb (last read
+//       by x2).
+// FX, the x-component of the flux, stays in registers: x2 and x3 map a thread to the same points.
+template <int D1, int TT, typename TC, typename TIO>
+struct TileLayout {
+    using TS = TileShape<D1, TT>;
+    static constexpr size_t A_BYTES = pad16((size_t)(TS::NA > TS::NQT ? TS::NA : TS::NQT) * sizeof(TC));
+    static constexpr size_t C_BYTES = pad16((size_t)TS::NC * sizeof(TC) > (size_t)TS::NS3 * sizeof(TIO)
+                                                ? (size_t)TS::NC * sizeof(TC) : (size_t)TS::NS3 * sizeof(TIO));
+    static constexpr size_t SEAM_ELEMS = (size_t)TS::NSX + TS::NSY + TS::NSZ;
+    size_t tb, codes, hd, a, c, fy, fz, total;
+    __host__ __device__ explicit TileLayout(int64_t tqs)
+    {
+        const size_t tb_bytes = pad16((size_t)tqs * sizeof(TC));
+        tb = 64;                                   // after the mbarrier
+        codes = tb + (tb_bytes > SEAM_ELEMS * sizeof(TC) ? tb_bytes : pad16(SEAM_ELEMS * sizeof(TC)));
+        hd = codes + pad16((size_t)TS::NS3 * 4);
+        a = hd + pad16((size_t)TS::NS3 * 4);
+        c = a + A_BYTES;
+        fy = c + C_BYTES;
+        fz = fy + pad16((size_t)TS::NQT * sizeof(TC));
+        total = fz + pad16((size_t)TS::NQT * sizeof(TC));
+    }
+};
+
 template <int D1, int TT, typename TC, typename TIO>
 __host__ __device__ inline size_t tile_smem_bytes(int64_t tqs, int /*Spad*/)
 {
-    using TS = TileShape<D1, TT>;
-    return 64 + pad16((size_t)tqs * sizeof(TC)) + 2 * pad16(TS::NS3 * 4) + pad16(TS::NS3 * sizeof(TIO)) +
-           pad16((size_t)TS::NA * sizeof(TC)) + pad16((size_t)TS::NC * sizeof(TC)) +
-           4 * pad16((size_t)TS::NQT * sizeof(TC)) +
-           pad16(((size_t)TS::NSX + (size_t)TS::NSY + (size_t)TS::NSZ) * sizeof(TC));
+    return TileLayout<D1, TT, TC, TIO>(tqs).total;
 }
 
 // n consecutive shared-memory values into registers; 16-byte vector loads when n % 4 == 0 (FP32)
@@ -113,6 +137,19 @@ struct Colloc {
     static constexpr int SA = TS::SA, NLP = TS::NLP;
     __host__ __device__ static constexpr int pidx(int qx, int qy, int qz) { return qz + QT * (qy + QT * qx); }
 
+    // out[q] = sum_a B[q][a] in[a], each sum in ascending a; the Q1 sums advance together so that
+    // their multiply-adds are independent of one another
+    template <typename TC>
+    __host__ __device__ static void interpolate(const BasisT<TC> &Bs, const TC (&in)[D1], TC (&out)[Q1])
+    {
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) out[q] = TC(0);
+#pragma unroll
+        for (int a = 0; a < D1; ++a)
+#pragma unroll
+            for (int q = 0; q < Q1; ++q) out[q] += Bs.B[q * D1 + a] * in[a];
+    }
+
     template <typename TC, typename TIO>
     __host__ __device__ static void z(const BasisT<TC> &Bs, const TIO *Vs, TC *A, int tid)
     {
@@ -122,13 +159,10 @@ struct Colloc {
         TC in[D1];
 #pragma unroll
         for (int a = 0; a < D1; ++a) in[a] = (TC)Vs[((K * h + a) * SE + sy) * SE + sx];
+        TC acc[Q1];
+        interpolate(Bs, in, acc);
 #pragma unroll
-        for (int q = 0; q < Q1; ++q) {
-            TC acc = TC(0);
-#pragma unroll
-            for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * in[a];
-            A[sx + SE * (Q1 * h + q) + SA * sy] = acc;
-        }
+        for (int q = 0; q < Q1; ++q) A[sx + SE * (Q1 * h + q) + SA * sy] = acc[q];
     }
 
     template <typename TC>
@@ -140,13 +174,10 @@ struct Colloc {
         TC in[D1];
 #pragma unroll
         for (int a = 0; a < D1; ++a) in[a] = A[sx + SE * qz + SA * (K * h + a)];
+        TC acc[Q1];
+        interpolate(Bs, in, acc);
 #pragma unroll
-        for (int q = 0; q < Q1; ++q) {
-            TC acc = TC(0);
-#pragma unroll
-            for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * in[a];
-            C[sx + SE * qz + SE * QT * (Q1 * h + q)] = acc;
-        }
+        for (int q = 0; q < Q1; ++q) C[sx + SE * qz + SE * QT * (Q1 * h + q)] = acc[q];
     }
 
     template <typename TC>
@@ -159,19 +190,17 @@ struct Colloc {
         TC in[D1];
 #pragma unroll
         for (int a = 0; a < D1; ++a) in[a] = C[xo + a];
+        TC acc[Q1];
+        interpolate(Bs, in, acc);
 #pragma unroll
-        for (int q = 0; q < Q1; ++q) {
-            TC acc = TC(0);
-#pragma unroll
-            for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * in[a];
-            U[pidx(Q1 * h + q, qy, qz)] = acc;
-        }
+        for (int q = 0; q < Q1; ++q) U[pidx(Q1 * h + q, qy, qz)] = acc[q];
     }
 
     // Tb: the tile's tangent block, layout [6][ex][qy][qz][qx] (qx element-local), components
     // xx yy zz xy xz yz of the symmetric dq/dg
+    // fx: this thread's x-flux at its Q1 points (registers in the kernel), read back by x3
     template <typename TC>
-    __host__ __device__ static void x2(const BasisT<TC> &Bs, const TC *Tb, const TC *U, TC *FX, TC *FY, TC *FZ,
+    __host__ __device__ static void x2(const BasisT<TC> &Bs, const TC *Tb, const TC *U, TC *fx, TC *FY, TC *FZ,
                                        int tid)
     {
         const int L = tid % NLP, h = tid / NLP;
@@ -182,26 +211,33 @@ struct Colloc {
         TC u[Q1];
 #pragma unroll
         for (int j = 0; j < Q1; ++j) u[j] = U[pidx(Q1 * h + j, qy, qz)];
+        // the 3 Q1 gradient sums (each in ascending j) advance together
+        TC gxs[Q1], gys[Q1], gzs[Q1];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) { gxs[q] = TC(0); gys[q] = TC(0); gzs[q] = TC(0); }
+#pragma unroll
+        for (int j = 0; j < Q1; ++j)
+#pragma unroll
+            for (int q = 0; q < Q1; ++q) {
+                const int qx = Q1 * h + q;
+                gxs[q] += Bs.Dc[q * Q1 + j] * u[j];
+                gys[q] += Bs.Dc[yl * Q1 + j] * U[pidx(qx, y0 + j, qz)];
+                gzs[q] += Bs.Dc[zl * Q1 + j] * U[pidx(qx, qy, z0 + j)];
+            }
 #pragma unroll
         for (int q = 0; q < Q1; ++q) {
             const int qx = Q1 * h + q;
-            TC gx = TC(0), gy = TC(0), gz = TC(0);
-#pragma unroll
-            for (int j = 0; j < Q1; ++j) {
-                gx += Bs.Dc[q * Q1 + j] * u[j];
-                gy += Bs.Dc[yl * Q1 + j] * U[pidx(qx, y0 + j, qz)];
-                gz += Bs.Dc[zl * Q1 + j] * U[pidx(qx, qy, z0 + j)];
-            }
+            const TC gx = gxs[q], gy = gys[q], gz = gzs[q];
             const TC txx = Tl[q], tyy = Tl[NQT + q], tzz = Tl[2 * NQT + q];
             const TC txy = Tl[3 * NQT + q], txz = Tl[4 * NQT + q], tyz = Tl[5 * NQT + q];
-            FX[pidx(qx, qy, qz)] = txx * gx + txy * gy + txz * gz;
+            fx[q] = txx * gx + txy * gy + txz * gz;
             FY[pidx(qx, qy, qz)] = txy * gx + tyy * gy + tyz * gz;
             FZ[pidx(qx, qy, qz)] = txz * gx + tyz * gy + tzz * gz;
         }
     }
 
     template <typename TC>
-    __host__ __device__ static void x3(const BasisT<TC> &Bs, const TC *FX, const TC *FY, const TC *FZ, TC *C,
+    __host__ __device__ static void x3(const BasisT<TC> &Bs, const TC *fx, const TC *FY, const TC *FZ, TC *C,
                                        TC *SX, int tid)
     {
         const int L = tid % NLP, h = tid / NLP;
@@ -209,22 +245,26 @@ struct Colloc {
         const int qz = L % QT, qy = L / QT;
         const int y0 = Q1 * (qy / Q1), yl = qy % Q1, z0 = Q1 * (qz / Q1), zl = qz % Q1;
         const int xo = SE * qz + SE * QT * qy + K * h;
+        // the Q1 sums W[q] (each over j ascending, x then y then z term) advance together
+        TC w[Q1];
+#pragma unroll
+        for (int q = 0; q < Q1; ++q) w[q] = TC(0);
+#pragma unroll
+        for (int j = 0; j < Q1; ++j)
+#pragma unroll
+            for (int q = 0; q < Q1; ++q) {
+                const int qx = Q1 * h + q;
+                w[q] += Bs.Dc[j * Q1 + q] * fx[j];
+                w[q] += Bs.Dc[j * Q1 + yl] * FY[pidx(qx, y0 + j, qz)];
+                w[q] += Bs.Dc[j * Q1 + zl] * FZ[pidx(qx, qy, z0 + j)];
+            }
         TC d[D1];
 #pragma unroll
         for (int a = 0; a < D1; ++a) d[a] = TC(0);
 #pragma unroll
-        for (int q = 0; q < Q1; ++q) {
-            const int qx = Q1 * h + q;
-            TC w = TC(0);
+        for (int q = 0; q < Q1; ++q)
 #pragma unroll
-            for (int j = 0; j < Q1; ++j) {
-                w += Bs.Dc[j * Q1 + q] * FX[pidx(Q1 * h + j, qy, qz)];
-                w += Bs.Dc[j * Q1 + yl] * FY[pidx(qx, y0 + j, qz)];
-                w += Bs.Dc[j * Q1 + zl] * FZ[pidx(qx, qy, z0 + j)];
-            }
-#pragma unroll
-            for (int a = 0; a < D1; ++a) d[a] += Bs.B[q * D1 + a] * w;
-        }
+            for (int a = 0; a < D1; ++a) d[a] += Bs.B[q * D1 + a] * w[q];
 #pragma unroll
         for (int a = 0; a < K; ++a) C[xo + a] = d[a];
         if (h == TT - 1) C[xo + K] = d[K];
@@ -337,7 +377,7 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
 {
     using TS = TileShape<D1, TT>;
     using S = Colloc<D1, TT>;
-    constexpr int NS3 = TS::NS3, NA = TS::NA, NC = TS::NC, NQT = TS::NQT, NSX = TS::NSX, NSY = TS::NSY;
+    constexpr int NS3 = TS::NS3, NSX = TS::NSX, NSY = TS::NSY;
     constexpr int NTH = TS::THREADS;
     if (P.skip && *P.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -346,19 +386,18 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
     const int64_t tqs = tq_stride<TC>(P);
     const uint32_t tq_bytes = (uint32_t)(tqs * sizeof(TC));
 
-    unsigned char *p = smem;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(p);    p += 64;
-    TC *Tb = reinterpret_cast<TC *>(p);                 p += pad16(tq_bytes);
-    uint32_t *codes = reinterpret_cast<uint32_t *>(p);  p += pad16(NS3 * 4);
-    uint32_t *hd = reinterpret_cast<uint32_t *>(p);     p += pad16(NS3 * 4);
-    TIO *Vs = reinterpret_cast<TIO *>(p);               p += pad16(NS3 * sizeof(TIO));
-    TC *A = reinterpret_cast<TC *>(p);                  p += pad16((size_t)NA * sizeof(TC));
-    TC *C = reinterpret_cast<TC *>(p);                  p += pad16((size_t)NC * sizeof(TC));
-    TC *U = reinterpret_cast<TC *>(p);                  p += pad16((size_t)NQT * sizeof(TC));
-    TC *FX = reinterpret_cast<TC *>(p);                 p += pad16((size_t)NQT * sizeof(TC));
-    TC *FY = reinterpret_cast<TC *>(p);                 p += pad16((size_t)NQT * sizeof(TC));
-    TC *FZ = reinterpret_cast<TC *>(p);                 p += pad16((size_t)NQT * sizeof(TC));
-    TC *SX = reinterpret_cast<TC *>(p);
+    const TileLayout<D1, TT, TC, TIO> lay(tqs);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    TC *Tb = reinterpret_cast<TC *>(smem + lay.tb);
+    uint32_t *codes = reinterpret_cast<uint32_t *>(smem + lay.codes);
+    uint32_t *hd = reinterpret_cast<uint32_t *>(smem + lay.hd);
+    TC *A = reinterpret_cast<TC *>(smem + lay.a);
+    TC *U = A;                                          // x1 .. x2
+    TC *C = reinterpret_cast<TC *>(smem + lay.c);
+    TIO *Vs = reinterpret_cast<TIO *>(smem + lay.c);    // prologue .. z
+    TC *FY = reinterpret_cast<TC *>(smem + lay.fy);
+    TC *FZ = reinterpret_cast<TC *>(smem + lay.fz);
+    TC *SX = Tb;                                        // x3 .. seam
     TC *SY = SX + NSX;
     TC *SZ = SY + NSY;
 
@@ -409,9 +448,10 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
     __syncthreads();
     S::x1(Bs, C, U, tid);
     __syncthreads();
-    S::x2(Bs, Tb, U, FX, FY, FZ, tid);
+    TC fx[D1];
+    S::x2(Bs, Tb, U, fx, FY, FZ, tid);
     __syncthreads();
-    S::x3(Bs, FX, FY, FZ, C, SX, tid);
+    S::x3(Bs, fx, FY, FZ, C, SX, tid);
     __syncthreads();
     S::yT(Bs, C, SX, A, SY, tid);
     __syncthreads();

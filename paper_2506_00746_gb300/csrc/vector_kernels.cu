@@ -32,9 +32,9 @@ __global__ void k_geometry(const GeomParams G, const double *__restrict__ vert, 
     int64_t ex[3] = { 0, 0, 0 };
     bool valid = true;
     for (int d = 0; d < dim; ++d) {
-        const int64_t Tc = tr % G.nt; tr /= G.nt;
+        const int64_t Tc = tr % G.nt[d]; tr /= G.nt[d];
         ex[d] = Tc * G.T + ec[d];
-        if (ex[d] >= G.n) valid = false;
+        if (ex[d] >= G.n[d]) valid = false;
     }
     double *ge = geo + eint * (int64_t)(ng * nq);
     if (!valid) {
@@ -44,12 +44,12 @@ __global__ void k_geometry(const GeomParams G, const double *__restrict__ vert, 
     const int qi[3] = { q % q1, (q / q1) % q1, dim == 3 ? q / (q1 * q1) : 0 };
     double xi[3] = { G.xq[qi[0]], G.xq[qi[1]], dim == 3 ? G.xq[qi[2]] : 0.0 };
     double w = G.wq[qi[0]] * G.wq[qi[1]] * (dim == 3 ? G.wq[qi[2]] : 1.0);
-    const int64_t nv = G.n + 1;
+    const int64_t nvx = G.n[0] + 1, nvy = G.n[1] + 1;
     double J[3][3] = { { 0, 0, 0 }, { 0, 0, 0 }, { 0, 0, 0 } }, x[3] = { 0, 0, 0 };
     const int ncorner = dim == 3 ? 8 : 4;
     for (int c = 0; c < ncorner; ++c) {
         const int cb[3] = { c & 1, (c >> 1) & 1, (c >> 2) & 1 };
-        const int64_t vi = (ex[0] + cb[0]) + nv * ((ex[1] + cb[1]) + (dim == 3 ? nv * (ex[2] + cb[2]) : 0));
+        const int64_t vi = (ex[0] + cb[0]) + nvx * ((ex[1] + cb[1]) + (dim == 3 ? nvy * (ex[2] + cb[2]) : 0));
         double sh[3], dsh[3];
         for (int d = 0; d < 3; ++d) {
             sh[d] = d < dim ? (cb[d] ? xi[d] : 1.0 - xi[d]) : 1.0;
@@ -122,20 +122,21 @@ __global__ void k_node_coords(const GeomParams G, int k, const double *__restric
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nl) return;
     const int dim = G.dim;
-    const int64_t m = (int64_t)k * G.n + 1, nv = G.n + 1;
-    int64_t gi[3] = { g % m, (g / m) % m, dim == 3 ? g / (m * m) : 0 };
+    const int64_t mx = (int64_t)k * G.n[0] + 1, my = (int64_t)k * G.n[1] + 1;
+    const int64_t nvx = G.n[0] + 1, nvy = G.n[1] + 1;
+    int64_t gi[3] = { g % mx, (g / mx) % my, dim == 3 ? g / (mx * my) : 0 };
     int64_t ex[3] = { 0, 0, 0 };
     double xi[3] = { 0, 0, 0 };
     for (int d = 0; d < dim; ++d) {
         int64_t e = gi[d] / k;
-        if (e >= G.n) e = G.n - 1;
+        if (e >= G.n[d]) e = G.n[d] - 1;
         ex[d] = e;
         xi[d] = G.xn[gi[d] - k * e];
     }
     double x[3] = { 0, 0, 0 };
     for (int c = 0; c < (dim == 3 ? 8 : 4); ++c) {
         const int cb[3] = { c & 1, (c >> 1) & 1, (c >> 2) & 1 };
-        const int64_t vi = (ex[0] + cb[0]) + nv * ((ex[1] + cb[1]) + (dim == 3 ? nv * (ex[2] + cb[2]) : 0));
+        const int64_t vi = (ex[0] + cb[0]) + nvx * ((ex[1] + cb[1]) + (dim == 3 ? nvy * (ex[2] + cb[2]) : 0));
         double sh = 1.0;
         for (int d = 0; d < dim; ++d) sh *= cb[d] ? xi[d] : 1.0 - xi[d];
         for (int a = 0; a < dim; ++a) x[a] += sh * vert[vi * dim + a];
@@ -157,12 +158,12 @@ __global__ void k_design_factors(const GeomParams G, const double *__restrict__ 
     int64_t tr = t, ex[3] = { 0, 0, 0 };
     bool valid = true;
     for (int d = 0; d < dim; ++d) {
-        const int64_t Tc = tr % G.nt; tr /= G.nt;
+        const int64_t Tc = tr % G.nt[d]; tr /= G.nt[d];
         ex[d] = Tc * G.T + ec[d];
-        if (ex[d] >= G.n) valid = false;
+        if (ex[d] >= G.n[d]) valid = false;
     }
     if (!valid) { kr[eint] = 1.0; dkr[eint] = 0.0; return; }
-    const int64_t e = ex[0] + G.n * (ex[1] + (dim == 3 ? (int64_t)G.n * ex[2] : 0));
+    const int64_t e = ex[0] + G.n[0] * (ex[1] + (dim == 3 ? (int64_t)G.n[1] * ex[2] : 0));
     const double r = rho[e];
     kr[eint] = kappa_eps + pow(r, kappa_q);
     dkr[eint] = kappa_q * pow(r, kappa_q - 1.0);
@@ -354,6 +355,51 @@ __global__ void k_waxpy(double *__restrict__ y, const double *__restrict__ a, do
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a[i] + alpha * b[i];
+}
+
+// y = alpha x + beta y (beta == 0: y is not read)
+__global__ void k_axpby(double alpha, const double *__restrict__ x, double beta, double *__restrict__ y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = beta == 0.0 ? alpha * x[i] : alpha * x[i] + beta * y[i];
+}
+
+// z = d .* r
+__global__ void k_mul(const double *__restrict__ d, const double *__restrict__ r, double *__restrict__ z, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = d[i] * r[i];
+}
+
+// y = 1 / x
+__global__ void k_recip(const double *__restrict__ x, double *__restrict__ y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = 1.0 / x[i];
+}
+
+// One face of the DOF lattice m[0] x m[1] x m[2] (axis = face / 2 held at 0 or m[axis] - 1): its
+// DOFs in lexicographic order of the two other axes (lower axis fastest).  y[g] += buf[i] on the
+// face's non-essential DOFs (a DOF is essential when it lies on a box face whose bit is clear in
+// `natural`).
+__global__ void k_face_add(FaceParams F, double *__restrict__ y, const double *__restrict__ buf)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ax = F.face / 2, a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+    const int64_t n1 = F.m[a1], n2 = F.m[a2];
+    if (i >= n1 * n2) return;
+    int64_t c[3];
+    c[ax] = (F.face & 1) ? F.m[ax] - 1 : 0;
+    c[a1] = i % n1;
+    c[a2] = i / n1;
+    bool ess = false;
+    for (int d = 0; d < F.dim; ++d) {
+        if (c[d] == 0 && !((F.natural >> (2 * d)) & 1)) ess = true;
+        if (c[d] == F.m[d] - 1 && !((F.natural >> (2 * d + 1)) & 1)) ess = true;
+    }
+    if (ess) return;
+    const int64_t g = c[0] + F.m[0] * (c[1] + F.m[1] * c[2]);
+    y[g] += buf[i];
 }
 
 // y = alpha x

@@ -22,6 +22,16 @@ struct CgState {
     double scalar;         // result slot of plain dot products
 };
 
+// One face of a context's DOF lattice (see k_face_add).
+struct FaceParams {
+    int dim, face, natural;
+    int64_t m[3];
+};
+
+__global__ void k_axpby(double alpha, const double *__restrict__ x, double beta, double *__restrict__ y, int64_t n);
+__global__ void k_mul(const double *__restrict__ d, const double *__restrict__ r, double *__restrict__ z, int64_t n);
+__global__ void k_recip(const double *__restrict__ x, double *__restrict__ y, int64_t n);
+__global__ void k_face_add(FaceParams F, double *__restrict__ y, const double *__restrict__ buf);
 __global__ void k_geometry(const GeomParams G, const double *__restrict__ vert, double *__restrict__ geo,
                            int *__restrict__ err);
 __global__ void k_node_coords(const GeomParams G, int k, const double *__restrict__ vert, double *__restrict__ xyz,

@@ -1,8 +1,9 @@
 // Host run of the collocated tile stages (Colloc<D1, TT> of the generic FP64 / double-float tile
 // kernel) against a per-element tensor-product Jacobian action on the same tile.  Each stage is a
 // host-callable function of the thread index; a loop over the thread indices runs it between the
-// same barriers as the kernel.  Random slot values and a random symmetric tangent per point; every
-// work array sits between guard regions (an access outside reads a huge sentinel or overwrites
+// same barriers as the kernel, once with the threads of each stage in ascending and once in
+// descending order, in the kernel's shared-memory aliasing (TileLayout).  Random slot values and a
+// random symmetric tangent per point; every work array sits between guard regions (an access outside reads a huge sentinel or overwrites
 // one) and starts as NaN (a read of an unwritten entry shows in the result).  Checks, per tile
 // shape: agreement with the reference to 1e-13 of its largest entry, every slot written exactly
 // once, no guard touched, every output finite.  Also: the collocation derivative table is exact on
@@ -20,10 +21,11 @@ void lagrange_tables(const std::vector<double> &nodes, const std::vector<double>
 using namespace feod;
 
 template <int D1, int TT>
-double run(unsigned seed)
+double run(unsigned seed, bool reverse)
 {
     using TS = TileShape<D1, TT>;
     using S = Colloc<D1, TT>;
+    using L = TileLayout<D1, TT, double, double>;
     constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT, NS3 = TS::NS3;
     BasisT<double> Bs{};
     std::vector<double> gx, gw, nodes, val, der, cval, cder;
@@ -52,12 +54,18 @@ double run(unsigned seed)
         for (int i = 0; i < n; ++i) store.back()[GRD + i] = fill;
         return store.size() - 1;
     };
-    const size_t iA = arr(TS::NA, nan), iC = arr(TS::NC, nan), iU = arr(NQT, nan), iFX = arr(NQT, nan),
-                 iFY = arr(NQT, nan), iFZ = arr(NQT, nan), iSX = arr(TS::NSX, nan), iSY = arr(TS::NSY, nan),
-                 iSZ = arr(TS::NSZ, nan);
+    // the kernel's aliasing: U inside A, the gathered block inside C, the seam planes inside the
+    // tangent block (region sizes as TileLayout allocates them)
+    const int nTb = (int)(std::max(L(6 * NQT).codes - L(6 * NQT).tb, L::SEAM_ELEMS * sizeof(double)) / sizeof(double));
+    const size_t iA = arr((int)(L::A_BYTES / sizeof(double)), nan), iC = arr((int)(L::C_BYTES / sizeof(double)), nan),
+                 iTb = arr(nTb, nan), iFY = arr(NQT, nan), iFZ = arr(NQT, nan);
     auto P_ = [&](size_t i) { return store[i].data() + GRD; };
-    double *A = P_(iA), *C = P_(iC), *Uq = P_(iU), *FX = P_(iFX), *FY = P_(iFY), *FZ = P_(iFZ);
-    double *SX = P_(iSX), *SY = P_(iSY), *SZ = P_(iSZ);
+    double *A = P_(iA), *C = P_(iC), *Tbs = P_(iTb), *FY = P_(iFY), *FZ = P_(iFZ);
+    double *Uq = A, *Vss = C;
+    double *SX = Tbs, *SY = SX + TS::NSX, *SZ = SY + TS::NSY;
+    for (int s = 0; s < NS3; ++s) Vss[s] = Vs[s];
+    for (int i = 0; i < 6 * NQT; ++i) Tbs[i] = Tb[i];
+    std::vector<double> fxs((size_t)TS::THREADS * Q1, nan);     // each thread's registers
     std::vector<uint32_t> codes(NS3), hd(NS3, 0);
     for (int s = 0; s < NS3; ++s) codes[s] = (uint32_t)s;
     std::vector<double> v(NS3, 0.0), y(NS3, nan), halo(1, 0.0), out0(TS::THREADS, 0.0);
@@ -67,14 +75,19 @@ double run(unsigned seed)
         void operator()(int s, double val) const { cnt[s]++; w(s, val); }
     } write{ SlotWriter<double, double>{ codes.data(), hd.data(), v.data(), y.data(), halo.data() }, writes.data() };
     const int NT = TS::THREADS;
-    for (int t = 0; t < NT; ++t) S::z(Bs, Vs.data(), A, t);
-    for (int t = 0; t < NT; ++t) S::y(Bs, A, C, t);
-    for (int t = 0; t < NT; ++t) S::x1(Bs, C, Uq, t);
-    for (int t = 0; t < NT; ++t) S::x2(Bs, Tb.data(), Uq, FX, FY, FZ, t);
-    for (int t = 0; t < NT; ++t) S::x3(Bs, FX, FY, FZ, C, SX, t);
-    for (int t = 0; t < NT; ++t) S::yT(Bs, C, SX, A, SY, t);
-    for (int t = 0; t < NT; ++t) S::zT(Bs, A, SY, SZ, write, out0[t], t);
-    for (int t = 0; t < NT; ++t) S::seam(SZ, write, out0[t], t);
+    // threads of a stage in ascending or descending order: a write of one thread that another
+    // thread of the same stage still reads shows in one of the two orders
+    auto each = [&](auto &&stage) {
+        for (int i = 0; i < NT; ++i) stage(reverse ? NT - 1 - i : i);
+    };
+    each([&](int t) { S::z(Bs, Vss, A, t); });
+    each([&](int t) { S::y(Bs, A, C, t); });
+    each([&](int t) { S::x1(Bs, C, Uq, t); });
+    each([&](int t) { S::x2(Bs, Tbs, Uq, fxs.data() + (size_t)t * Q1, FY, FZ, t); });
+    each([&](int t) { S::x3(Bs, fxs.data() + (size_t)t * Q1, FY, FZ, C, SX, t); });
+    each([&](int t) { S::yT(Bs, C, SX, A, SY, t); });
+    each([&](int t) { S::zT(Bs, A, SY, SZ, write, out0[t], t); });
+    each([&](int t) { S::seam(SZ, write, out0[t], t); });
     // reference: per element, full tensor products
     std::vector<double> yr(NS3, 0.0);
     for (int ez = 0; ez < TT; ++ez) for (int ey = 0; ey < TT; ++ey) for (int ex = 0; ex < TT; ++ex)
@@ -109,8 +122,9 @@ double run(unsigned seed)
         nrm = std::max(nrm, std::fabs(yr[s]));
         if (writes[s] != 1) ++bad_writes;
     }
-    printf("D1=%d TT=%d threads=%d  max|y-yref|/max|yref| = %.3e  slots written != once: %d  guards hit: %d  "
-           "non-finite: %d\n", D1, TT, NT, err / nrm, bad_writes, guards, nonfinite);
+    printf("D1=%d TT=%d threads=%d %s  max|y-yref|/max|yref| = %.3e  slots written != once: %d  guards hit: %d  "
+           "non-finite: %d\n", D1, TT, NT, reverse ? "descending" : "ascending ", err / nrm, bad_writes, guards,
+           nonfinite);
     return (bad_writes == 0 && guards == 0 && nonfinite == 0 && err / nrm < 1e-13) ? 0.0 : 1.0;
 }
 
@@ -150,8 +164,11 @@ int main()
 {
     double bad = 0;
     for (int q1 = 2; q1 <= 7; ++q1) bad += check_dc(q1);
-    bad += run<2, 4>(1); bad += run<3, 3>(2); bad += run<4, 2>(3); bad += run<5, 2>(4); bad += run<6, 2>(5);
-    bad += run<7, 1>(6); bad += run<2, 1>(7); bad += run<3, 2>(8); bad += run<4, 1>(9); bad += run<5, 1>(10);
+    for (bool rev : { false, true }) {
+        bad += run<2, 4>(1, rev); bad += run<3, 3>(2, rev); bad += run<4, 2>(3, rev); bad += run<5, 2>(4, rev);
+        bad += run<6, 2>(5, rev); bad += run<7, 1>(6, rev); bad += run<2, 1>(7, rev); bad += run<3, 2>(8, rev);
+        bad += run<4, 1>(9, rev); bad += run<5, 1>(10, rev);
+    }
     printf(bad == 0 ? "ALL OK\n" : "FAILURES\n");
     return bad == 0 ? 0 : 1;
 }

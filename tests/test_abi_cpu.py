@@ -48,13 +48,32 @@ def test_binding_matches_header(lib_path):
         assert hasattr(lib, name)
 
 
+def _header_struct_fields(name: str) -> list[str]:
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", src, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            fields.append(re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[\d+\])?\s*$", decl)[0])
+    return fields
+
+
+@pytest.mark.parametrize("name", ["fe_mesh", "fe_problem", "fe_setup_opts", "fe_newton_opts", "fe_batch_item",
+                                  "fe_batch_opts"])
+def test_binding_structs_match_header(name):
+    """The ctypes structures list the header's fields in the header's order."""
+    from paper_2506_00746_gb300 import abi
+    assert [f[0] for f in getattr(abi, name)._fields_] == _header_struct_fields(name)
+
+
 def test_setup_rejects_bad_arguments_without_gpu(lib_path):
     """Argument validation happens before any device call."""
     import ctypes
     from paper_2506_00746_gb300 import abi
     lib = abi.library(lib_path)
     V = np.zeros((4, 2))
-    mesh = abi.fe_mesh(2, 1, V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    mesh = abi.make_mesh(2, 1, V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     prob = abi.fe_problem(3.0, 0.0, 0, 1.0, None, 0.0, 1.0)
     ctx = ctypes.c_void_p()
     assert lib.fe_setup(ctypes.byref(mesh), 0, 0, ctypes.byref(prob), ctypes.byref(ctx)) == 5   # order 0
@@ -64,6 +83,11 @@ def test_setup_rejects_bad_arguments_without_gpu(lib_path):
     assert lib.fe_setup(ctypes.byref(mesh), 2, 0, ctypes.byref(bad), ctypes.byref(ctx)) == 1
     assert b"p >= 2" in lib.fe_last_error(None)
     assert lib.fe_setup(None, 2, 0, ctypes.byref(prob), ctypes.byref(ctx)) == 1
+    bad_mesh = abi.make_mesh(2, (1, 0), V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))   # n[1] = 0
+    assert lib.fe_setup(ctypes.byref(bad_mesh), 2, 0, ctypes.byref(prob), ctypes.byref(ctx)) == 1
+    bad_faces = abi.make_mesh(2, 1, V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), natural_faces=16)  # z- in 2D
+    assert lib.fe_setup(ctypes.byref(bad_faces), 2, 0, ctypes.byref(prob), ctypes.byref(ctx)) == 1
+    assert b"natural_faces" in lib.fe_last_error(None)
     assert not ctx.value
     assert lib.fe_status_string(2) == b"invalid mesh (det J <= 0)"
     o = abi.fe_newton_default_opts()

@@ -33,7 +33,11 @@ def _rel(a, b):
 
 
 def _call(lib, fn, ctx, v, y, precision, stream):
-    return getattr(lib, fn)(ctx, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(y.data_ptr()), precision, stream)
+    """fe_jacobian_action (cached linearisation: u = NULL) or fe_jacobian_action_noalloc."""
+    vp, yp = ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(y.data_ptr())
+    if fn == "fe_jacobian_action":
+        return lib.fe_jacobian_action(ctx, None, vp, yp, precision, stream)
+    return getattr(lib, fn)(ctx, vp, yp, precision, stream)
 
 
 @pytest.mark.parametrize("dim,n,k", [(3, 6, 3), (2, 16, 2), (3, 5, 2)])
