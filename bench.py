@@ -544,11 +544,11 @@ def run_split(args) -> dict | None:
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (each rank: the seeded jittered 64^3 lattice shifted in z, seeded state and direction)",
-        "config": {"workload": f"{args.workload} per rank: 3D p-Laplacian p=3, 64 x 64 x {64 * world} hex lattice split "
-                               f"in {world} z-slabs, order 3, {part.n_dofs} DOFs; step = one split FP64 J(u) v "
-                               "(local action + one interface exchange)",
+        "config": {"workload": f"{args.workload} per rank: 3D p-Laplacian p={w.p:g}, {w.n} x {w.n} x {w.n * world} hex "
+                               f"lattice split in {world} z-slabs, order {w.order}, {part.n_dofs} DOFs; step = one "
+                               "split FP64 J(u) v (local action + one interface exchange)",
                    "n_dofs": part.n_dofs, "parallelism": f"subdomain split P over {world} ranks ({args.backend})",
-                   "l2": "inputs larger than L2 (FP64 tangent 805 MB per rank)"},
+                   "l2": "FP64 tangent %.0f MB per rank" % (6 * 8 * w.n ** 3 * (w.order + 1) ** 3 / 1e6)},
         "gpu_launches": int(launches), "clocks": clocks,
         "jv_mixed_gdofs": round(part.n_dofs * args.steps / t32 / 1e9, 4),
         "e2e": {"value": round(part.n_dofs * args.steps / t_e2e / 1e9, 4), "unit": "GDOF/s",
@@ -723,8 +723,35 @@ def run_design(args) -> dict:
            "forward_newton_s": round(t_fwd, 4), "adjoint_backward_s": round(t_bwd, 4),
            "fd_directions": args.fd_dirs, "fd_step": h, "fd_rel_err_max": max(errs),
            "fd_rel_err_median": float(np.median(errs)), "fd_time_s": round(t_fd, 3)}
+    # the same Newton solve by the FP64 GPU path and by the mixed-precision one, to 1e-8
+    for name, prec in (("fp64", 64), ("mixed", -32)):
+        op.set_design(torch.from_numpy(rho0).cuda())
+        u = u0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = op.newton_solve(u, rtol=1e-8, inner_precision=prec, raise_on_error=False)
+        torch.cuda.synchronize()
+        out[f"newton_{name}"] = {"time_s": round(time.perf_counter() - t0, 4), "status": rep["status"],
+                                 "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"], "rel": rep["rel"]}
     op.close()
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = design_cpu_baseline(w, V, rho0)
     return out
+
+
+def design_cpu_baseline(w, V, rho0) -> dict:
+    """The oracle's Newton solve of the design case on the host cores (assembled sparse Jacobian,
+    Jacobi-preconditioned scipy CG to 1e-4 per step, the GPU's line search), to 1e-8."""
+    import oracle as O
+    from paper_2506_00746_gb300 import inputs as I
+    cores = O.set_threads(os.cpu_count() or 1)
+    P = O.Problem(3, w.n, w.order, V, p=w.p, eps=w.eps, rho=rho0)
+    its: list = []
+    t0 = time.perf_counter()
+    _, hist = O.newton(P, I.smooth_field(3, w.n, w.order, seed=w.state_seed), rtol=1e-8, linear="cg", cg_iters=its)
+    return {"kind": "oracle", "cores": cores, "newton_time_s": round(time.perf_counter() - t0, 3),
+            "newton_iters": len(hist) - 1, "cg_iters": int(sum(its)), "rel_residual": float(hist[-1] / hist[0]),
+            "sample": "the whole 48^3 order-2 design problem"}
 
 
 def run_batched(args) -> dict:

@@ -105,7 +105,9 @@ fe_status fe_setup(const fe_mesh *mesh, int order, int q1d, const fe_problem *pr
 fe_status fe_setup_ex(const fe_mesh *mesh, int order, int q1d, const fe_problem *prob,
                       const fe_setup_opts *opts, fe_ctx **out);
 
-/* Number of DOFs N_L, free (non-essential) DOFs and elements. */
+/* Sizes of the decomposition's vectors (Fig. 1): N_L, the DOFs of the L-vector (on one GPU the
+ * T-vector too), the free (non-essential) DOFs among them, and the elements N_e (the E-vector has
+ * N_e (k+1)^dim entries, the Q-vector N_e (k+1)^dim points). */
 fe_status fe_num_dofs(const fe_ctx *ctx, int64_t *n_l, int64_t *n_free);
 fe_status fe_num_elements(const fe_ctx *ctx, int64_t *n_e);
 
@@ -197,7 +199,9 @@ fe_status fe_node_coords(fe_ctx *ctx, double *xyz, void *stream);
  * stream).  Invalidates the cached linearisation. */
 fe_status fe_set_design(fe_ctx *ctx, const double *rho, void *stream);
 
-/* fe_adjoint_vjp: per-element design gradient of the residual contracted with lambda,
+/* fe_adjoint_vjp (Section 2, the design-sensitivity paragraph after Eq. 3: derivatives of a
+ * PDE-constrained objective by the adjoint method, with AD applied locally at the quadrature
+ * points): per-element design gradient of the residual contracted with lambda,
  *   grad_rho[e] = lambda^T dR/drho_e = kappa_rho'(rho_e) int_e kappa(|grad u|) grad u . grad lambda,
  * obtained by seeding a dual number on rho at each quadrature point (AD local to the quadrature
  * point; no scatter, element-local reduction).  For the compliance c = F^T u with R(u; rho) = 0,
@@ -205,6 +209,21 @@ fe_status fe_set_design(fe_ctx *ctx, const double *rho, void *stream);
  * u, lambda: device double[N_L]; grad_rho: device double[N_e] (element order ex fastest). */
 fe_status fe_adjoint_vjp(fe_ctx *ctx, const double *u, const double *lambda, double *grad_rho,
                          void *stream);
+
+/* fe_compliance: the design problem's objective c = F^T u (F the load vector, zero on essential
+ * DOFs), written to the DEVICE double *c; summed in a fixed order.  The compliance of Section 2's
+ * design example (Fig. 2).  u: device double[N_L]. */
+fe_status fe_compliance(fe_ctx *ctx, const double *u, double *c, void *stream);
+
+/* fe_compliance_gradient: grad_rho = scale * dc/drho at the solution u of R(u; rho) = 0, by the
+ * adjoint method of the paragraph after Eq. 3: linearise at u (fe_linearize), solve J(u) lambda = F
+ * (J symmetric) by Jacobi-preconditioned CG to ||r|| <= rtol ||F|| in `precision` (as
+ * fe_cg_solve's), then grad_rho = -scale lambda^T dR/drho (fe_adjoint_vjp's kernel).  Needs a
+ * design field; replaces the cached linearisation by the one at u.  u: device double[N_L];
+ * grad_rho: device double[N_e]; iters (may be NULL): the CG iterations.  Synchronous.  Errors as
+ * fe_cg_solve's. */
+fe_status fe_compliance_gradient(fe_ctx *ctx, const double *u, double scale, double rtol, int max_iter,
+                                 int precision, double *grad_rho, int *iters, void *stream);
 
 /* fe_element_matrices: dense element tangent matrices K_e = dr_e/du_e = B^T J_D(u_q) B (Eq. 3) of
  * the elements [e0, e0 + count) (lexicographic element order, x fastest) at the state u, each
@@ -261,7 +280,10 @@ typedef struct {
 
 fe_status fe_newton_default_opts(fe_newton_opts *opts);
 
-/* newton_solve: solve R(u) = 0 from u_inout (device double[N_L], carrying the boundary values),
+/* newton_solve (Section 2, closing remarks: the matrix-free nonlinear solver that the residual of
+ * Eq. 1 and the Jacobian action of Eq. 2 serve; the paper leaves its algorithm to later work, so
+ * the one below -- inexact Newton with CG and a backtracking line search -- is this library's
+ * reading): solve R(u) = 0 from u_inout (device double[N_L], carrying the boundary values),
  * overwritten with the solution.  Each step: R and J_D at u (fused, FP64 dual numbers), Jacobi-
  * preconditioned CG on J d = -R with the partially assembled J, then a backtracking line search
  * on ||R|| (R, its norm, u and the line search always FP64).  inner_precision 64: the CG runs in

@@ -324,8 +324,9 @@ def _compliance_autograd():
         """c(rho) = F^T u(rho) with R(u; rho) = 0, differentiable in rho by the adjoint method.
 
         forward: Newton solve from ``u0`` (the converged state is checkpointed, not the Newton
-        history); backward: adjoint CG J(u) lambda = F with the cached linearisation at u, then
-        dc/drho = -lambda^T dR/drho from the quadrature-point dual-number VJP kernel.
+        history), then fe_compliance; backward: fe_compliance_gradient at the checkpointed state
+        (adjoint CG J(u) lambda = F, then dc/drho = -lambda^T dR/drho from the quadrature-point
+        dual-number VJP kernel), scaled by the incoming gradient.
         """
 
         @staticmethod
@@ -333,20 +334,19 @@ def _compliance_autograd():
             op.set_design(rho.detach().contiguous())
             u = u0.detach().clone()
             op.newton_solve(u, **(newton_kw or {}))
-            F = op.load_vector()
-            c = torch.dot(F, u)
+            c = torch.empty((), dtype=torch.float64, device=op.device)
+            abi.fe_compliance(op.ctx, u, c)
             ctx.op = op
-            ctx.save_for_backward(u, F)
+            ctx.save_for_backward(u)
             return c
 
         @staticmethod
         def backward(ctx, grad_c):
-            u, F = ctx.saved_tensors
+            (u,) = ctx.saved_tensors
             op = ctx.op
-            op.linearize(u)
-            lam, _ = op.cg_solve(F, rtol=1e-12)
-            g = -op.adjoint_vjp(u, lam)
-            return grad_c * g, None, None, None
+            g = torch.empty(op.n_elements, dtype=torch.float64, device=op.device)
+            abi.fe_compliance_gradient(op.ctx, u, float(grad_c), 1e-12, 50000, 64, g)
+            return g, None, None, None
 
     return ComplianceFn
 

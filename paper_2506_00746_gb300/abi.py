@@ -114,6 +114,9 @@ _SIGS = {
     "fe_memory_bytes": (c_int, [_CTX, POINTER(c_int64)]),
     "fe_measure_fp64_peak": (c_int, [c_int, POINTER(c_double), POINTER(c_double), c_void_p]),
     "fe_dot": (c_int, [_CTX, c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
+    "fe_compliance": (c_int, [_CTX, c_void_p, c_void_p, c_void_p]),
+    "fe_compliance_gradient": (c_int, [_CTX, c_void_p, c_double, c_double, c_int, c_int, c_void_p, POINTER(c_int),
+                                       c_void_p]),
     "fe_axpby": (c_int, [_CTX, c_double, c_void_p, c_double, c_void_p, c_void_p]),
     "fe_pointwise_mul": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_void_p]),
     "fe_reciprocal": (c_int, [_CTX, c_void_p, c_void_p, c_void_p]),
@@ -324,6 +327,18 @@ def fe_measure_fp64_peak(reps: int = 20, stream=None) -> tuple[float, float]:
 def fe_dot(ctx, a, b, begin: int, end: int, out, stream=None):
     """out (a device double tensor of one entry) = a[begin:end] . b[begin:end]."""
     check(library().fe_dot(ctx, ptr(a), ptr(b), begin, end, ptr(out), stream_handle(stream)), "fe_dot", ctx)
+
+
+def fe_compliance(ctx, u, out, stream=None):
+    """out (a device double tensor of one entry) = F^T u."""
+    check(library().fe_compliance(ctx, ptr(u), ptr(out), stream_handle(stream)), "fe_compliance", ctx)
+
+
+def fe_compliance_gradient(ctx, u, scale: float, rtol: float, max_iter: int, precision: int, grad, stream=None) -> int:
+    it = c_int()
+    check(library().fe_compliance_gradient(ctx, ptr(u), scale, rtol, max_iter, precision, ptr(grad), byref(it),
+                                           stream_handle(stream)), "fe_compliance_gradient", ctx)
+    return it.value
 
 
 def fe_axpby(ctx, alpha: float, x, beta: float, y, stream=None):

@@ -914,6 +914,23 @@ extern "C" fe_status fe_adjoint_vjp(fe_ctx *c, const double *u, const double *la
     return FE_OK;
 }
 
+extern "C" fe_status fe_compliance(fe_ctx *c, const double *u, double *out, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!u || !out) return fail(c, FE_ERR_ARG, "fe_compliance: null vectors");
+    fe_status s = ensure_work(c);
+    if (s != FE_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    if ((s = fe_load_vector(c, c->w_r, stream)) != FE_OK) return s;
+    CgState *ds = cg_state(c) + 1;
+    {
+        LaunchScope ls(c, "dot", st);
+        k_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_r, u, c->nl, c->w_partial + 2 * RED_BLOCKS, &ds->counter, out);
+    }
+    CKLAUNCH();
+    return FE_OK;
+}
+
 // ------------------------------------------------------------------------------------------------
 // solvers
 // ------------------------------------------------------------------------------------------------
@@ -946,6 +963,30 @@ extern "C" fe_status fe_cg_solve(fe_ctx *c, const double *b, double *x, double r
     if (done == CG_BREAKDOWN) return fail(c, FE_ERR_BREAKDOWN, "CG breakdown (p^T J p <= 0)");
     if (done == CG_NAN) return fail(c, FE_ERR_NAN, "CG produced NaN/Inf");
     if (done == CG_MAXIT) return fail(c, FE_ERR_NOT_CONVERGED, "CG reached %d iterations", max_iter);
+    return FE_OK;
+}
+
+extern "C" fe_status fe_compliance_gradient(fe_ctx *c, const double *u, double scale, double rtol, int max_iter,
+                                            int precision, double *grad_rho, int *iters, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    if (!u || !grad_rho) return fail(c, FE_ERR_ARG, "fe_compliance_gradient: null vectors");
+    if (!c->has_rho) return fail(c, FE_ERR_STATE, "fe_compliance_gradient needs a design field");
+    fe_status s = ensure_work(c);
+    if (s != FE_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    // J(u) lambda = F: the load vector in w_r, lambda in w_d (fe_cg_solve works in its own vectors)
+    if ((s = fe_linearize(c, u, stream)) != FE_OK) return s;
+    if ((s = fe_load_vector(c, c->w_r, stream)) != FE_OK) return s;
+    if ((s = fe_cg_solve(c, c->w_r, c->w_d, rtol, max_iter, precision, iters, stream)) != FE_OK) return s;
+    // fe_cg_solve ran on the context's own stream and synchronised it; the rest on `stream`
+    c->ops->vjp(c, u, c->w_d, grad_rho, st);
+    CKLAUNCH();
+    {
+        LaunchScope ls(c, "scale", st);
+        k_scale<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(grad_rho, grad_rho, -scale, c->ne);
+    }
+    CKLAUNCH();
     return FE_OK;
 }
 

@@ -117,6 +117,17 @@ def test_compliance_gradient_against_fd():
     lam = O.adjoint_solve(P, u_ref)
     g_ref = -O.adjoint_grad(P, u_ref, lam)
     assert np.linalg.norm(g.cpu().numpy() - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
+    # the objective c = F^T u (fe_compliance) against the oracle's load vector and solution
+    F_ref = O.load(P)
+    F_ref[O.essential(P)] = 0.0
+    assert abs(c.item() - F_ref @ u_ref) <= 1e-10 * abs(F_ref @ u_ref)
+    # fe_compliance_gradient scales by the incoming gradient
+    from paper_2506_00746_gb300 import abi
+    u = u0.clone()
+    op.newton_solve(u, **kw)
+    g2 = torch.empty_like(g)
+    abi.fe_compliance_gradient(op.ctx, u, -0.5, 1e-12, 50000, 64, g2)
+    assert torch.linalg.norm(g2 + 0.5 * g) <= 1e-12 * torch.linalg.norm(g)
     rng = np.random.default_rng(4)
     h = 1e-5
     for _ in range(4):
