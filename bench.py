@@ -784,6 +784,12 @@ def run_batched(args) -> dict:
     l0 = B.shape()["launches"]
     t_b = _event_time(lambda: B.jacobian_action(v, out=y), args.steps, args.warmup)
     launches = (B.shape()["launches"] - l0) / (args.steps + args.warmup)
+    # the same action captured once in a CUDA graph and replayed
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        B.jacobian_action(v, out=y)
+    t_graph = _event_time(graph.replay, args.steps, args.warmup)
     # the same instances one after another through their own single-instance operators
     ops = [Operator(3, d["n"], d["order"], d["vertices"], p=d["p"]) for d in inst]
     vs, ys = [], []
@@ -814,6 +820,7 @@ def run_batched(args) -> dict:
            "launch": B.shape(), "create_and_tune_s": round(t_create, 3),
            "batched_jv_ms": round(t_b * 1e3, 4), "batched_jv_gdofs": round(total_dofs / t_b / 1e9, 3),
            "batched_jv_launches_per_step": launches,
+           "batched_jv_graph_ms": round(t_graph * 1e3, 4),
            "batched_jv_hbm_frac": round(bytes_alg / t_b / 1e9 / peaks["hbm_gbs"], 4),
            "sequential_jv_ms": round(t_s * 1e3, 4), "sequential_jv_gdofs": round(total_dofs / t_s / 1e9, 3),
            "sequential_jv_launches_per_step": 2 * len(ws),

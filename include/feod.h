@@ -122,8 +122,14 @@ fe_status fe_linearize(fe_ctx *ctx, const double *u, void *stream);
 
 /* Device-side failures: every wait inside a kernel is bounded.  One that times out (a tile's
  * tangent copy that does not land) abandons that kernel's work and sets the context's error word;
- * the next synchronous call on the context (fe_jacobian_action_host, fe_cg_solve, newton_solve)
- * returns FE_ERR_CUDA and clears the word. */
+ * the next synchronous call on the context (fe_jacobian_action_host, fe_cg_solve, newton_solve,
+ * fe_check_error) returns FE_ERR_CUDA and clears the word.  Results computed by the failed kernel
+ * and by everything queued after it on the context are invalid until that check: callers of the
+ * asynchronous calls (fe_residual, fe_jacobian_action, ...) read the word with fe_check_error. */
+
+/* fe_check_error: synchronise `stream`, then return FE_ERR_CUDA (and clear the word) if a kernel
+ * of this context has reported a timed-out wait since the last check, else FE_OK. */
+fe_status fe_check_error(fe_ctx *ctx, void *stream);
 
 /* fe_selftest_wait_timeout: diagnostic of that path.  Runs one CTA whose bounded wait on an
  * mbarrier phase that nothing completes (no arrival, no copy) gives up after about a second and

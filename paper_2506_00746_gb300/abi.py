@@ -127,6 +127,7 @@ _SIGS = {
     "fe_status_string": (c_char_p, [c_int]),
     "fe_element_matrices": (c_int, [_CTX, c_void_p, c_int, c_int64, c_int64, c_void_p, c_void_p]),
     "fe_selftest_wait_timeout": (c_int, [_CTX, c_void_p]),
+    "fe_check_error": (c_int, [_CTX, c_void_p]),
     "fe_batch_create": (c_int, [POINTER(fe_batch_item), c_int, POINTER(fe_batch_opts), POINTER(_BATCH)]),
     "fe_batch_info": (c_int, [_BATCH, c_int, POINTER(c_int64), POINTER(c_int64), POINTER(c_int)]),
     "fe_batch_shape": (c_int, [_BATCH, POINTER(c_int64), POINTER(c_int), POINTER(c_int), POINTER(c_int),
@@ -254,6 +255,11 @@ def fe_adjoint_vjp(ctx, u, lam, grad, stream=None):
 def fe_element_matrices(ctx, u, method: int, e0: int, count: int, K, stream=None):
     check(library().fe_element_matrices(ctx, ptr(u), method, e0, count, ptr(K), stream_handle(stream)),
           "fe_element_matrices", ctx)
+
+
+def fe_check_error(ctx, stream=None):
+    """Raise FeodError (FE_ERR_CUDA) if a kernel of the context reported a timed-out wait."""
+    check(library().fe_check_error(ctx, stream_handle(stream)), "fe_check_error", ctx)
 
 
 def fe_selftest_wait_timeout(ctx, stream=None):

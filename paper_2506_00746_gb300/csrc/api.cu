@@ -151,6 +151,7 @@ fe_status ensure_work(fe_ctx *c)
     CK(dalloc(c, &c->w_cr, n));
     CK(dalloc(c, &c->w_cp, n));
     CK(dalloc(c, &c->w_cq, n));
+    CK(dalloc(c, &c->w_cz, n));
     CK(dalloc(c, &c->w_fx, n));
     CK(dalloc(c, &c->w_fr, n));
     CK(dalloc(c, &c->w_fp, n));
@@ -245,8 +246,8 @@ void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
             else if (precision == 48) c->ops->jv_pa_df(c, c->w_cp, c->w_cq, st);
             else c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
             { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
-            { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_dinv64, n, s, c->w_partial); }
-            { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cp, c->w_cr, c->w_dinv64, n, s); }
+            { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cr, c->w_cq, c->w_dinv64, c->w_cz, n, s, c->w_partial); }
+            { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cx, c->w_cp, c->w_cz, n, s); }
         } else {
             c->ops->jv_pa_32(c, c->w_fp, c->w_fq, st);
             { LaunchScope ls(c, "cg_alpha32", st); k_cg_alpha32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_fp, c->w_fq, n, s, c->w_partial); }
@@ -562,19 +563,36 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
             slot[(size_t)t * c->Spad + s] = code;
         }
     }
-    // The cross-tile partial sums are stored compactly in fix-up order: sorted by DOF, then by
-    // tile; the partial of halo slot (t, s) goes to hdst[t][s], and DOF fix_g[r] adds the run
-    // [fix_off[r], fix_off[r+1]) of them to its owner's value, in ascending tile order.
+    // The cross-tile partial sums are stored compactly in fix-up order: one row per DOF that
+    // several tiles share, holding the non-owning tiles' partials in ascending tile order.  Rows
+    // are grouped by their length (1, 3, 7: the DOF lies on 1, 2 or 3 interior tile planes), each
+    // group sorted by DOF.  The partial of halo slot (t, s) goes to hdst[t][s], and the fix-up
+    // adds row r to the owner's value y[fix_g[r]] in that order (fix_entries gives the row's
+    // place).
     std::sort(halo_pairs.begin(), halo_pairs.end());
-    std::vector<uint32_t> fix_g, fix_off, hdst((size_t)c->ntiles * c->Spad, 0u);
-    for (size_t i = 0; i < halo_pairs.size(); ++i) {
-        const uint32_t g = (uint32_t)(halo_pairs[i] >> 32);
-        if (fix_g.empty() || fix_g.back() != g) { fix_g.push_back(g); fix_off.push_back((uint32_t)i); }
-        hdst[halo_pairs[i] & 0xFFFFFFFFu] = (uint32_t)i;
+    std::vector<uint32_t> fix_g, hdst((size_t)c->ntiles * c->Spad, 0u);
+    {
+        std::vector<std::pair<size_t, size_t>> runs[3];      // [begin, end) in halo_pairs, by class
+        for (size_t i = 0; i < halo_pairs.size();) {
+            size_t j = i;
+            while (j < halo_pairs.size() && (halo_pairs[j] >> 32) == (halo_pairs[i] >> 32)) ++j;
+            const size_t cnt = j - i;
+            const int cls = cnt == 1 ? 0 : cnt == 3 ? 1 : cnt == 7 ? 2 : -1;
+            if (cls < 0) return fail(c, FE_ERR_UNSUPPORTED, "a DOF has %zu cross-tile partial sums", cnt);
+            runs[cls].push_back({ i, j });
+            i = j;
+        }
+        uint32_t pos = 0;
+        for (int cls = 0; cls < 3; ++cls)
+            for (const auto &rn : runs[cls]) {
+                fix_g.push_back((uint32_t)(halo_pairs[rn.first] >> 32));
+                for (size_t i = rn.first; i < rn.second; ++i) hdst[halo_pairs[i] & 0xFFFFFFFFu] = pos++;
+            }
+        c->fix.n1 = (int64_t)runs[0].size();
+        c->fix.n3 = (int64_t)runs[1].size();
+        c->nfixh = (int64_t)pos;
     }
-    fix_off.push_back((uint32_t)halo_pairs.size());
     c->nfix = (int64_t)fix_g.size();
-    c->nfixh = (int64_t)halo_pairs.size();
 
     // --- 1D rules and basis tables on [0,1] ---
     std::vector<double> gx, gw, nodes, val, der;
@@ -618,11 +636,9 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     CK(dalloc(c, &c->d_slot, slot.size()));
     CK(cudaMemcpy(c->d_slot, slot.data(), slot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_fix_g, fix_g.size()));
-    CK(dalloc(c, &c->d_fix_off, fix_off.size()));
     CK(dalloc(c, &c->d_hdst, hdst.size()));
     CK(cudaMemcpy(c->d_hdst, hdst.data(), hdst.size() * 4, cudaMemcpyHostToDevice));
     if (!fix_g.empty()) CK(cudaMemcpy(c->d_fix_g, fix_g.data(), fix_g.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->d_fix_off, fix_off.data(), fix_off.size() * 4, cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_vert, (size_t)nvert * dim));
     CK(cudaMemcpy(c->d_vert, mesh->vertices, (size_t)nvert * dim * sizeof(double), cudaMemcpyHostToDevice));
     CK(dalloc(c, &c->d_geo, (size_t)c->nepad * c->NG * c->NQ));
@@ -664,7 +680,7 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     c->op.kr = c->d_kr; c->op.dkr = c->d_dkr; c->op.skip = nullptr;
     c->op.law_a = 0.5 * (prob->p - 2.0); c->op.eps2 = prob->eps * prob->eps;
     c->op.hdst = c->d_hdst;
-    c->fix.nfix = c->nfix; c->fix.fix_g = c->d_fix_g; c->fix.fix_off = c->d_fix_off;
+    c->fix.nfix = c->nfix; c->fix.fix_g = c->d_fix_g;
     c->fix.skip = nullptr;
     CK(c->ops->prepare(c));
     CK(cudaDeviceSynchronize());
@@ -710,9 +726,9 @@ extern "C" fe_status fe_setup_ex(const fe_mesh *mesh, int order, int q1d, const 
 extern "C" void fe_destroy(fe_ctx *c)
 {
     if (!c) return;
-    void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_fix_off, c->d_hdst, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
+    void *ptrs[] = { c->d_gt_off, c->d_gt_src, c->d_slot, c->d_fix_g, c->d_hdst, c->d_vert, c->d_geo, c->d_rho, c->d_kr,
                      c->d_dkr, c->d_T64, c->d_T32, c->d_Tdf, c->d_diag, c->d_halo, c->d_err, c->w_r, c->w_d, c->w_trial,
-                     c->w_dinv, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_fx, c->w_fr, c->w_fp, c->w_fq, c->w_state, c->w_partial };
+                     c->w_dinv, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, c->w_cq, c->w_cz, c->w_fx, c->w_fr, c->w_fp, c->w_fq, c->w_state, c->w_partial };
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
@@ -832,6 +848,12 @@ extern "C" fe_status fe_jacobian_action_host(fe_ctx *c, const void *v_host, void
     if (s != FE_OK) return s;
     CK(cudaMemcpyAsync(y_host, dy, es * (size_t)c->nl, cudaMemcpyDeviceToHost, st));
     return check_device_error(c, st);
+}
+
+extern "C" fe_status fe_check_error(fe_ctx *c, void *stream)
+{
+    if (!c) return FE_ERR_ARG;
+    return check_device_error(c, as_stream(stream));
 }
 
 extern "C" fe_status fe_selftest_wait_timeout(fe_ctx *c, void *stream)

@@ -282,9 +282,11 @@ __global__ void k_fixup_batch(const BatchFix *__restrict__ bf, const int64_t *__
         const BatchFix &B = bf[lo];
         if (B.fix.skip && *B.fix.skip) continue;
         const int64_t rr = r - row0[lo];
+        uint32_t first, cnt;
+        fix_entries(B.fix, rr, first, cnt);
         g[i] = B.fix.fix_g[rr];
-        j0[i] = B.fix.fix_off[rr];
-        j1[i] = B.fix.fix_off[rr + 1];
+        j0[i] = first;
+        j1[i] = first + cnt;
         yp[i] = yb + B.off;
         hp[i] = B.halo;
     }

@@ -275,7 +275,7 @@ enum OutMode { OUT_JV = 0, OUT_RES = 1, OUT_DIAG = 2 };
 // G^T inside the tile, then the write: every slot sums the contributions of the (at most 2 per
 // direction) elements that contain it, in ascending (z, y, x) element order.  Owned slots are
 // written (essential rows: J v -> v_i, residual -> 0, diagonal -> 1); halo slots go to
-// halo[t*S + s] for the fix-up kernel.
+// halo[hdst[t][s]] for the fix-up kernel.
 template <int DIM, int D1, typename TC, typename TIO, int OUT>
 __device__ __forceinline__ void scatter_tile(const OpParams &P, int64_t t, const TileInfo &ti, const TC *Ye,
                                              TIO *__restrict__ y, const TIO *__restrict__ vorig,
@@ -330,8 +330,9 @@ __device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddep
 
 // Fix-up: y[g] = y[g] + sum of the halo partial sums of g, in ascending tile order, accumulated
 // in the compute type TC.  Each thread takes FIX_ROWS rows (the rows of one load round are
-// consecutive across a warp) and issues the loads of all its rows before it uses them: the
-// kernel is bound by the latency of its dependent loads (row index -> value, halo entries).
+// consecutive across a warp) and issues the loads of all its rows before it uses them; a row's
+// halo entries sit at an address that follows from the row number, so they load together with
+// the row's DOF, and the kernel waits for the owner's value (DOF -> y) and one halo round.
 // Every CTA allows the dependent launch at once, so that a programmatically launched tile kernel
 // after it (the next Jacobian action) is scheduled into the SMs its last CTAs free; that kernel
 // waits for this grid before it reads or writes anything this one touches.
@@ -347,9 +348,11 @@ __global__ void k_fixup(const FixParams F, const TC *__restrict__ halo, TIO *__r
     for (int i = 0; i < FIX_ROWS; ++i) {
         const int64_t r = r0 + (int64_t)i * blockDim.x;
         const bool ok = r < F.nfix;
+        uint32_t first = 0u, count = 0u;
+        if (ok) fix_entries(F, r, first, count);
         g[i] = ok ? F.fix_g[r] : 0u;
-        j0[i] = ok ? F.fix_off[r] : 0u;
-        j1[i] = ok ? F.fix_off[r + 1] : 0u;
+        j0[i] = first;
+        j1[i] = first + count;
     }
     TC acc[FIX_ROWS];
     uint32_t kmax = 0;

@@ -87,14 +87,24 @@ struct OpParams {
     double eps2;      // eps^2
 };
 
-// Fix-up (deterministic G^T across tiles): y[fix_g[r]] += sum_j halo[j], j in [off[r], off[r+1]),
-// the partial sums of the non-owning tiles stored contiguously in ascending tile order
+// Fix-up (deterministic G^T across tiles): y[fix_g[r]] += row r's halo entries, the partial sums
+// of the non-owning tiles, stored contiguously in ascending tile order.  A DOF on m interior tile
+// planes has 2^m - 1 non-owning tiles, so the rows come in runs by length: n1 rows of 1 entry (a
+// tile face), then n3 rows of 3 (a tile edge), then the rest of 7 (a tile corner), each run
+// sorted by DOF; a row's first entry follows from its number (fix_entries), so no offset table
+// is read.
 struct FixParams {
-    int64_t nfix;
+    int64_t nfix, n1, n3;
     const uint32_t *fix_g;
-    const uint32_t *fix_off;
     const int *skip;
 };
+
+__host__ __device__ inline void fix_entries(const FixParams &F, int64_t r, uint32_t &first, uint32_t &count)
+{
+    if (r < F.n1) { first = (uint32_t)r; count = 1u; }
+    else if (r < F.n1 + F.n3) { first = (uint32_t)(F.n1 + 3 * (r - F.n1)); count = 3u; }
+    else { first = (uint32_t)(F.n1 + 3 * F.n3 + 7 * (r - F.n1 - F.n3)); count = 7u; }
+}
 
 // Geometry setup parameters.
 struct GeomParams {
@@ -168,7 +178,7 @@ struct fe_ctx {
 
     // device arrays
     uint32_t *d_slot = nullptr;
-    uint32_t *d_fix_g = nullptr, *d_fix_off = nullptr, *d_hdst = nullptr;
+    uint32_t *d_fix_g = nullptr, *d_hdst = nullptr;
     int64_t nfix = 0, nfixh = 0;
     double *d_vert = nullptr;
     double *d_geo = nullptr;
@@ -188,6 +198,7 @@ struct fe_ctx {
     float *w_dinv = nullptr;      // Jacobi scaling 1/diag(J), FP32
     double *w_dinv64 = nullptr;   // the same values in FP64 (the FP64 CG kernels' operand)
     double *w_cx = nullptr, *w_cr = nullptr, *w_cp = nullptr, *w_cq = nullptr;   // FP64 CG
+    double *w_cz = nullptr;       // FP64 CG: the preconditioned residual dinv r
     float *w_fx = nullptr, *w_fr = nullptr, *w_fp = nullptr, *w_fq = nullptr;    // FP32 CG
     void *w_state = nullptr;      // device CG state
     double *w_partial = nullptr;  // reduction partials

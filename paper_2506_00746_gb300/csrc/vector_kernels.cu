@@ -255,6 +255,7 @@ __global__ void k_cg_init(const double *__restrict__ b, const double *__restrict
         st->rz = o[0]; st->rr = o[1]; st->rr0 = o[1];
         st->tol2 = rtol * rtol * o[1];
         st->iter = 0; st->max_iter = max_iter;
+        st->xpend = 0;
         st->done = (o[1] <= st->tol2 || o[1] == 0.0) ? CG_CONVERGED : (isfinite(o[1]) ? 0 : CG_NAN);
         if (max_iter <= 0 && !st->done) st->done = CG_MAXIT;
     }
@@ -288,10 +289,11 @@ __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restric
     }
 }
 
-// x += alpha p; r -= alpha q; z = dinv r; rz' = r.z, rr = r.r; beta = rz'/rz; convergence test.
-__global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, CgState *st,
-                            double *partial)
+// r -= alpha q; z = dinv r (stored); rz' = r.z, rr = r.r; beta = rz'/rz; convergence test.  The
+// matching update of x (x += alpha p) is left to k_cg_direction, which reads p anyway: xpend says
+// it is due, also in the iteration that converges.
+__global__ void k_cg_update(double *__restrict__ r, const double *__restrict__ q, const double *__restrict__ dinv,
+                            double *__restrict__ z, int64_t n, CgState *st, double *partial)
 {
     if (st->done) return;
     __shared__ double sh[RED_THREADS];
@@ -299,20 +301,21 @@ __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, cons
     double s[2] = { 0.0, 0.0 };
     const int64_t gs = (int64_t)gridDim.x * RED_THREADS;
     for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += BATCH * gs) {
-        double xv[BATCH], pv[BATCH], rv[BATCH], qv[BATCH], dv[BATCH];
+        double rv[BATCH], qv[BATCH], dv[BATCH];
 #pragma unroll
         for (int u = 0; u < BATCH; ++u) {
             const int64_t j = i + u * gs;
-            if (j < n) { xv[u] = x[j]; pv[u] = p[j]; rv[u] = r[j]; qv[u] = q[j]; dv[u] = dinv[j]; }
+            if (j < n) { rv[u] = r[j]; qv[u] = q[j]; dv[u] = dinv[j]; }
         }
 #pragma unroll
         for (int u = 0; u < BATCH; ++u) {
             const int64_t j = i + u * gs;
             if (j < n) {
-                x[j] = xv[u] + alpha * pv[u];
                 const double ri = rv[u] - alpha * qv[u];
+                const double zi = dv[u] * ri;
                 r[j] = ri;
-                s[0] += ri * dv[u] * ri; s[1] += ri * ri;
+                z[j] = zi;
+                s[0] += ri * zi; s[1] += ri * ri;
             }
         }
     }
@@ -321,30 +324,51 @@ __global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, cons
         st->beta = o[0] / st->rz;
         st->rz = o[0]; st->rr = o[1];
         st->iter += 1;
+        st->xpend = 1;
         if (!isfinite(o[1])) st->done = CG_NAN;
         else if (o[1] <= st->tol2) st->done = CG_CONVERGED;
         else if (st->iter >= st->max_iter) st->done = CG_MAXIT;
     }
 }
 
-// p = dinv r + beta p (skipped once converged).
-__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
-                               int64_t n, const CgState *st)
+// x += alpha p (the update of the last k_cg_update, when xpend says it is due), then, unless the
+// CG has stopped, p = z + beta p.  The last block (by ticket) clears xpend: every block has read it
+// before it takes its ticket.
+__global__ void __launch_bounds__(VEC_THREADS, 4) k_cg_direction(double *__restrict__ x, double *__restrict__ p,
+                                                                  const double *__restrict__ z, int64_t n,
+                                                                  CgState *st)
 {
-    if (st->done) return;
-    const double beta = st->beta;
+    if (!st->xpend) return;
+    const double alpha = st->alpha, beta = st->beta;
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += BATCH * gs) {
-        double rv[BATCH], pv[BATCH], dv[BATCH];
+    if (st->done == 0) {
+#pragma unroll 1
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += BATCH * gs) {
+            double xv[BATCH], pv[BATCH], zv[BATCH];
 #pragma unroll
-        for (int u = 0; u < BATCH; ++u) {
-            const int64_t j = i + u * gs;
-            if (j < n) { dv[u] = dinv[j]; rv[u] = r[j]; pv[u] = p[j]; }
+            for (int u = 0; u < BATCH; ++u) {
+                const int64_t j = i + u * gs;
+                if (j < n) { xv[u] = x[j]; pv[u] = p[j]; zv[u] = z[j]; }
+            }
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                const int64_t j = i + u * gs;
+                if (j < n) {
+                    x[j] = xv[u] + alpha * pv[u];
+                    p[j] = zv[u] + beta * pv[u];
+                }
+            }
         }
-#pragma unroll
-        for (int u = 0; u < BATCH; ++u) {
-            const int64_t j = i + u * gs;
-            if (j < n) p[j] = dv[u] * rv[u] + beta * pv[u];
+    } else {
+        // the CG has stopped: only the last iteration's x update remains
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) x[i] = x[i] + alpha * p[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(&st->counter, 1u);
+        if (ticket == gridDim.x - 1) {
+            st->xpend = 0;
+            st->counter = 0u;
         }
     }
 }

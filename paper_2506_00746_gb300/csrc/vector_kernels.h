@@ -20,6 +20,7 @@ struct CgState {
     unsigned counter;      // last-block ticket of the reductions (returns to 0 after each)
     int scale_exp;         // FP32 CG: the system is solved for b / 2^scale_exp
     double scalar;         // result slot of plain dot products
+    int xpend;             // FP64-vector CG: the x update of the last iteration is still due
 };
 
 // One face of a context's DOF lattice (see k_face_add).
@@ -45,11 +46,10 @@ __global__ void k_cg_init(const double *__restrict__ b, const double *__restrict
                           int max_iter, double *partial);
 __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restrict__ q, int64_t n, CgState *st,
                            double *partial);
-__global__ void k_cg_update(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, CgState *st,
-                            double *partial);
-__global__ void k_cg_direction(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
-                               int64_t n, const CgState *st);
+__global__ void k_cg_update(double *__restrict__ r, const double *__restrict__ q, const double *__restrict__ dinv,
+                            double *__restrict__ z, int64_t n, CgState *st, double *partial);
+__global__ void k_cg_direction(double *__restrict__ x, double *__restrict__ p, const double *__restrict__ z,
+                               int64_t n, CgState *st);
 __global__ void k_waxpy(double *__restrict__ y, const double *__restrict__ a, double alpha,
                         const double *__restrict__ b, int64_t n);
 __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, double alpha, int64_t n);

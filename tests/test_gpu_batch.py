@@ -102,6 +102,33 @@ def test_batch_policies_bitwise_equal():
     assert torch.equal(ys[0], ys[1]) and torch.equal(ys[0], ys[2])
 
 
+@pytest.mark.parametrize("policy", [0, 3])
+def test_batch_jv_captured_in_a_graph(policy):
+    """The batched action captured in a CUDA graph (its launches on torch's capture stream) and
+    replayed: bit for bit the direct call's result, on two different directions."""
+    import torch
+    from paper_2506_00746_gb300 import Batch
+    inst = _instances()
+    B = Batch(inst, tune=False, tiles=[4, 2, 2, 2], policy=policy)
+    B.linearize(B.concat(_states(inst)))
+    v = B.concat([I.uniform_vector(n, seed=300 + i) for i, n in enumerate(B.n_dofs)], torch.float32)
+    y = torch.zeros_like(v)                            # the gaps between instances stay zero
+    B.jacobian_action(v, out=y)                        # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.jacobian_action(v, out=y)
+    for seed in (400, 500):
+        w = B.concat([I.uniform_vector(n, seed=seed + i) for i, n in enumerate(B.n_dofs)], torch.float32)
+        v.copy_(w)
+        g.replay()
+        torch.cuda.synchronize()
+        ref = B.jacobian_action(w)
+        for a, b in zip(B.split(y), B.split(ref)):
+            assert torch.equal(a, b)
+    B.close()
+
+
 def test_batch_newton_matches_oracle():
     import torch
     from paper_2506_00746_gb300 import Batch

@@ -179,7 +179,8 @@ def test_device_wait_timeout_is_reported_and_context_survives():
     y = op.jacobian_action(torch.from_numpy(v).cuda()).cpu().numpy()
     y_ref = O.jv(P, u0, v)
     assert np.linalg.norm(y - y_ref) <= 1e-12 * np.linalg.norm(y_ref)
-    # the word was cleared: a synchronous solve runs normally
+    # the word was cleared: fe_check_error finds nothing, a synchronous solve runs normally
+    abi.fe_check_error(op.ctx)
     u = ud.clone()
     assert op.newton_solve(u, rtol=1e-8)["status"] == "FE_OK"
     op.close()
