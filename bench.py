@@ -375,6 +375,7 @@ def run_gpu(args) -> dict | None:
     bytes32 = jv_algorithmic_bytes(nl, ne, nq, nq, 4)
     k32name = "k_jv_tile2<4,2,float>"
     traffic32, traffic32_src = profiled_traffic(k32name)
+    traffic_fix32, _ = profiled_traffic("k_fixup<float,float>")
     flops_res = residual_algorithmic_flops(w.dim, ne, w.order + 1, w.order + 1)
     out = {
         "metric": METRIC,
@@ -418,7 +419,10 @@ def run_gpu(args) -> dict | None:
                                 "kernel_achieved": round(bytes32 / t_main32 / 1e9, 1),
                                 "kernel_frac": round(bytes32 / t_main32 / 1e9 / peaks["hbm_gbs"], 4),
                                 "action_frac": round(bytes32 / (t32 / ncalls) / 1e9 / peaks["hbm_gbs"], 4),
-                                "traffic": traffic32, "traffic_summary": traffic32_src}},
+                                "traffic": traffic32, "fixup_traffic": traffic_fix32,
+                                "action_traffic_ratio": (round((traffic32 + traffic_fix32) / bytes32, 4)
+                                                         if traffic32 and traffic_fix32 else None),
+                                "traffic_summary": traffic32_src}},
         "jv_double_float_gdofs": round(nl * ncalls / tdf / 1e9, 4),
         "jv_cg_mixed_gdofs": round(nl * ncalls / tcg / 1e9, 4),
         "residual_f64": {"gdofs": round(nl * ncalls / tres / 1e9, 4), "kernel_ms": round(t_res_main * 1e3, 5),
