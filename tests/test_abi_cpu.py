@@ -88,6 +88,13 @@ def test_setup_rejects_bad_arguments_without_gpu(lib_path):
     bad_faces = abi.make_mesh(2, 1, V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), natural_faces=16)  # z- in 2D
     assert lib.fe_setup(ctypes.byref(bad_faces), 2, 0, ctypes.byref(prob), ctypes.byref(ctx)) == 1
     assert b"natural_faces" in lib.fe_last_error(None)
+    # the largest lattice: more than 2^30 - 1 DOFs is rejected before anything is read or allocated
+    # (the vertex array is never touched, so a small one stands in)
+    big = abi.make_mesh(3, (1100, 1100, 1100), V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    prob3 = abi.fe_problem(3.0, 0.0, 0, 1.0, None, 0.0, 1.0)
+    assert lib.fe_setup(ctypes.byref(big), 1, 0, ctypes.byref(prob3), ctypes.byref(ctx)) == 5
+    assert b"DOFs exceed" in lib.fe_last_error(None)
+    assert not ctx.value
     assert not ctx.value
     assert lib.fe_status_string(2) == b"invalid mesh (det J <= 0)"
     o = abi.fe_newton_default_opts()
