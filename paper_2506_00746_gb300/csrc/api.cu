@@ -681,7 +681,9 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
     c->op.law_a = 0.5 * (prob->p - 2.0); c->op.eps2 = prob->eps * prob->eps;
     c->op.hdst = c->d_hdst;
     c->fix.nfix = c->nfix; c->fix.fix_g = c->d_fix_g;
+    c->fix.r0 = 0; c->fix.r1 = c->nfix;
     c->fix.skip = nullptr;
+    c->h_fix_g = std::move(fix_g);
     CK(c->ops->prepare(c));
     CK(cudaDeviceSynchronize());
     return FE_OK;
@@ -732,6 +734,10 @@ extern "C" void fe_destroy(fe_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->cp_in) cudaStreamDestroy(c->cp_in);
+    if (c->cp_out) cudaStreamDestroy(c->cp_out);
+    for (cudaEvent_t e : c->chunk_ev)
+        if (e) cudaEventDestroy(e);
     for (auto &g : c->cg_loop_exec)
         if (g) cudaGraphExecDestroy(g);
     for (auto &g : c->cg_exec)
@@ -832,6 +838,77 @@ extern "C" fe_status fe_jacobian_action(fe_ctx *c, const double *u, const void *
     return FE_OK;
 }
 
+namespace {
+
+// The cached J v of a host vector in z-chunks of tile layers, so that the copies overlap the
+// kernels: chunk c's DOF planes go to the device on one stream, its tiles run on `st` once they
+// have landed, the fix-up rows of the planes that are then complete follow, and those planes go
+// back on a third stream.  A tile layer L reads the DOF planes k T L .. k T (L + 1); after the
+// layers below k T L1 have run (and the fix-up of their rows), the planes below k T L1 are final:
+// the plane k T L1 itself still waits for its owner, the first layer of the next chunk.  The
+// arithmetic is that of the one-piece action (the same kernels on the same tiles, the same
+// fix-up rows in the same order), so the result is the same bit for bit.
+fe_status jv_host_chunked(fe_ctx *c, const void *v_host, void *y_host, int precision, void *dv, void *dy,
+                          cudaStream_t st)
+{
+    const size_t es = precision == 32 ? sizeof(float) : sizeof(double);
+    const int64_t k = c->k, T = c->T;
+    const int64_t mxy = ((int64_t)k * c->n[0] + 1) * ((int64_t)k * c->n[1] + 1);
+    const int64_t zmax = (int64_t)k * c->n[2];                // last DOF plane
+    const int64_t ntz = c->nt[2], ntxy = (int64_t)c->nt[0] * c->nt[1];
+    const int nch = (int)std::min<int64_t>(8, ntz);
+    if (!c->cp_in) {
+        CK(cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking));
+        for (auto &e : c->chunk_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    // the rows of each length class (1, 3, 7 halo entries), sorted by DOF within the class
+    const int64_t cls0[3] = { 0, c->fix.n1, c->fix.n1 + c->fix.n3 };
+    const int64_t cls1[3] = { c->fix.n1, c->fix.n1 + c->fix.n3, c->nfix };
+    auto row_of = [&](int cl, int64_t g) {      // first row of class cl whose DOF is >= g
+        const uint32_t *b = c->h_fix_g.data() + cls0[cl], *e = c->h_fix_g.data() + cls1[cl];
+        return cls0[cl] + (int64_t)(std::lower_bound(b, e, (uint32_t)std::min<int64_t>(g, 0xFFFFFFFFll)) - b);
+    };
+    // the caller's stream work before this call, then the chunks
+    CK(cudaEventRecord(c->chunk_ev[0], st));
+    CK(cudaStreamWaitEvent(c->cp_in, c->chunk_ev[0], 0));
+    int64_t in_end = 0, fin_end = 0;      // planes [0, in_end) sent, [0, fin_end) final
+    for (int ch = 0; ch < nch; ++ch) {
+        const int64_t L0 = ntz * ch / nch, L1 = ntz * (ch + 1) / nch;
+        const bool last = ch == nch - 1;
+        const int64_t need = last ? zmax + 1 : std::min(k * T * L1, zmax) + 1;
+        const int64_t fin = last ? zmax + 1 : k * T * L1;
+        cudaEvent_t ein = c->chunk_ev[1 + 2 * (ch % 8)], efin = c->chunk_ev[2 + 2 * (ch % 8)];
+        if (need > in_end) {
+            CK(cudaMemcpyAsync((char *)dv + in_end * mxy * es, (const char *)v_host + in_end * mxy * es,
+                               (size_t)((need - in_end) * mxy) * es, cudaMemcpyHostToDevice, c->cp_in));
+            in_end = need;
+        }
+        CK(cudaEventRecord(ein, c->cp_in));
+        CK(cudaStreamWaitEvent(st, ein, 0));
+        c->ops->jv_tiles(c, precision, dv, dy, L0 * ntxy, (L1 - L0) * ntxy, st);
+        CKLAUNCH();
+        for (int cl = 0; cl < 3; ++cl) {
+            const int64_t r0 = row_of(cl, fin_end * mxy), r1 = row_of(cl, fin * mxy);
+            c->ops->fix_rows(c, precision, dy, r0, r1, st);
+        }
+        CKLAUNCH();
+        CK(cudaEventRecord(efin, st));
+        CK(cudaStreamWaitEvent(c->cp_out, efin, 0));
+        if (fin > fin_end) {
+            CK(cudaMemcpyAsync((char *)y_host + fin_end * mxy * es, (const char *)dy + fin_end * mxy * es,
+                               (size_t)((fin - fin_end) * mxy) * es, cudaMemcpyDeviceToHost, c->cp_out));
+            fin_end = fin;
+        }
+    }
+    // the copies back belong to the call: `st` waits for them
+    CK(cudaEventRecord(c->chunk_ev[0], c->cp_out));
+    CK(cudaStreamWaitEvent(st, c->chunk_ev[0], 0));
+    return FE_OK;
+}
+
+}  // namespace
+
 extern "C" fe_status fe_jacobian_action_host(fe_ctx *c, const void *v_host, void *y_host, int precision,
                                              void *stream)
 {
@@ -841,6 +918,18 @@ extern "C" fe_status fe_jacobian_action_host(fe_ctx *c, const void *v_host, void
     fe_status s = ensure_work(c);
     if (s != FE_OK) return s;
     cudaStream_t st = as_stream(stream);
+    // the tile kernels of 3D problems with several tile layers: chunks that overlap the copies
+    const int var = precision == 64 ? 0 : precision == 32 ? 1 : precision == -32 ? 2 : precision == 48 ? 3 : -1;
+    if (var >= 0 && c->dim == 3 && c->pipe_grid[var] > 0 && c->nt[2] >= 2 && c->chunked_host) {
+        if ((precision == 64 || precision == 48) && !c->lin64)
+            return fail(c, FE_ERR_STATE, "no FP64 linearisation cached (call fe_linearize)");
+        if ((precision == 32 || precision == -32) && !c->lin32)
+            return fail(c, FE_ERR_STATE, "no FP32 linearisation cached (call fe_linearize)");
+        if (precision == 48 && (s = prepare_tangent_df(c, st)) != FE_OK) return s;
+        s = jv_host_chunked(c, v_host, y_host, precision, c->w_trial, c->w_d, st);
+        if (s != FE_OK) return s;
+        return check_device_error(c, st);
+    }
     // staging in the CG work vectors (each holds N_L doubles)
     void *dv = c->w_trial, *dy = c->w_d;
     CK(cudaMemcpyAsync(dv, v_host, es * (size_t)c->nl, cudaMemcpyHostToDevice, st));

@@ -342,12 +342,12 @@ __global__ void k_fixup(const FixParams F, const TC *__restrict__ halo, TIO *__r
 {
     allow_dependent_launch();
     if (F.skip && *F.skip) return;
-    const int64_t r0 = (int64_t)blockIdx.x * FIX_ROWS * blockDim.x + threadIdx.x;
+    const int64_t r0 = F.r0 + (int64_t)blockIdx.x * FIX_ROWS * blockDim.x + threadIdx.x;
     uint32_t g[FIX_ROWS], j0[FIX_ROWS], j1[FIX_ROWS];
 #pragma unroll
     for (int i = 0; i < FIX_ROWS; ++i) {
         const int64_t r = r0 + (int64_t)i * blockDim.x;
-        const bool ok = r < F.nfix;
+        const bool ok = r < F.r1;
         uint32_t first = 0u, count = 0u;
         if (ok) fix_entries(F, r, first, count);
         g[i] = ok ? F.fix_g[r] : 0u;
@@ -1002,13 +1002,17 @@ struct Ops {
     static int nthreads(const fe_ctx *c) { return c->NE * SH::TEAM; }
 
     template <typename TC, typename TIO>
-    static void fixup(fe_ctx *c, TIO *y, cudaStream_t st)
+    static void fixup(fe_ctx *c, TIO *y, cudaStream_t st, int64_t r0 = 0, int64_t r1 = -1)
     {
-        if (c->nfix == 0) return;
+        if (r1 < 0) r1 = c->nfix;
+        if (r1 <= r0) return;
         LaunchScope ls(c, "fixup", st);
         const int bs = 256;
-        const int64_t nb = (c->nfix + (int64_t)bs * FIX_ROWS - 1) / ((int64_t)bs * FIX_ROWS);
-        k_fixup<TC, TIO><<<(unsigned)nb, bs, 0, st>>>(c->fix, reinterpret_cast<TC *>(c->d_halo), y);
+        const int64_t nb = (r1 - r0 + (int64_t)bs * FIX_ROWS - 1) / ((int64_t)bs * FIX_ROWS);
+        FixParams F = c->fix;
+        F.r0 = r0;
+        F.r1 = r1;
+        k_fixup<TC, TIO><<<(unsigned)nb, bs, 0, st>>>(F, reinterpret_cast<TC *>(c->d_halo), y);
     }
 
     static void residual(fe_ctx *c, const double *u, double *r, double *T64, float *T32, cudaStream_t st)
@@ -1114,6 +1118,47 @@ struct Ops {
         }
         return cudaSuccess;
     }
+    // the tile kernel alone on tiles [t0, t0 + nt) (3D, tile kernel enabled; plain launch)
+    template <typename TC, typename TIO>
+    static void jv_tile_range(fe_ctx *c, const TIO *v, TIO *y, int64_t t0, int64_t nt, cudaStream_t st)
+    {
+        if constexpr (DIM == 3) {
+            constexpr int TT = max_tile(3, D1 - 1);
+            if (nt <= 0) return;
+            OpParams P = c->op;
+            P.t0 = t0;
+            if constexpr (is_dfloat<TC>::value) {
+                LaunchScope ls(c, "jv_pa_df", st);
+                const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
+                k_jv_tile<D1, TT, TC, TIO><<<(unsigned)nt, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                    P, c->bdf, c->d_Tdf, v, y, reinterpret_cast<TC *>(c->d_halo));
+            } else if constexpr (sizeof(TC) == 8) {
+                LaunchScope ls(c, "jv_pa_f64", st);
+                const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
+                k_jv_tile<D1, TT, TC, TIO><<<(unsigned)nt, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                    P, c->b64, c->d_T64, v, y, reinterpret_cast<TC *>(c->d_halo));
+            } else {
+                LaunchScope ls(c, "jv_pa_f32", st);
+                const size_t tsm = tile2_smem_bytes<D1, TT, TIO>(c->tqs32);
+                k_jv_tile2<D1, TT, TIO><<<(unsigned)nt, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                    P, c->p32, c->d_T32, v, y, reinterpret_cast<float *>(c->d_halo));
+            }
+        }
+    }
+    static void jv_tiles(fe_ctx *c, int precision, const void *v, void *y, int64_t t0, int64_t nt, cudaStream_t st)
+    {
+        if (precision == 64) jv_tile_range<double, double>(c, (const double *)v, (double *)y, t0, nt, st);
+        else if (precision == 48) jv_tile_range<dfloat, double>(c, (const double *)v, (double *)y, t0, nt, st);
+        else if (precision == -32) jv_tile_range<float, double>(c, (const double *)v, (double *)y, t0, nt, st);
+        else jv_tile_range<float, float>(c, (const float *)v, (float *)y, t0, nt, st);
+    }
+    static void fix_rows(fe_ctx *c, int precision, void *y, int64_t r0, int64_t r1, cudaStream_t st)
+    {
+        if (precision == 64) fixup<double, double>(c, (double *)y, st, r0, r1);
+        else if (precision == 48) fixup<dfloat, double>(c, (double *)y, st, r0, r1);
+        else if (precision == -32) fixup<float, double>(c, (double *)y, st, r0, r1);
+        else fixup<float, float>(c, (float *)y, st, r0, r1);
+    }
     static void jv_pa_64(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<double, double>(c, v, y, st); }
     static void jv_pa_32(fe_ctx *c, const float *v, float *y, cudaStream_t st) { jv_pa<float, float>(c, v, y, st); }
     static void jv_pa_32d(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<float, double>(c, v, y, st); }
@@ -1207,7 +1252,7 @@ struct Ops {
     {
         static const OpTable t = { DIM, D1, residual, jv_pa_64, jv_pa_32, jv_pa_32d, jv_pa_df,
                                    jv_dual_64, jv_dual_32, jv_dual_32d, diag_64, diag_32, vjp,
-                                   prepare, max_smem };
+                                   prepare, max_smem, jv_tiles, fix_rows };
         return &t;
     }
 };

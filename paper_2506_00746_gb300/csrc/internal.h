@@ -72,6 +72,7 @@ struct OpParams {
     int Spad;         // per-tile stride of slot codes and halo entries (S rounded up to 4)
     int law;          // LawKind
     int64_t ntiles;
+    int64_t t0;       // first tile of a launch (the tile kernels take one tile per CTA from t0)
     int64_t tqs32;    // per-tile stride (floats) of the FP32 tangent, a multiple of 4
     int64_t tqs64;    // per-tile stride (doubles) of the FP64 tangent, a multiple of 2
     const uint32_t *slot;   // [ntiles][Spad]
@@ -95,6 +96,7 @@ struct OpParams {
 // is read.
 struct FixParams {
     int64_t nfix, n1, n3;
+    int64_t r0, r1;           // the rows a launch handles, [r0, r1) ([0, nfix) for the whole sum)
     const uint32_t *fix_g;
     const int *skip;
 };
@@ -144,6 +146,11 @@ struct OpTable {
     cudaError_t (*prepare)(fe_ctx *c);
     // bytes of dynamic shared memory of the largest kernel for tile size T
     size_t (*max_smem)(int S, int T);
+    // the cached J v in pieces (3D tile kernels only): the tile kernel on tiles [t0, t0 + nt),
+    // then the fix-up of rows [r0, r1); precision as fe_jacobian_action's (64, 48, 32, -32);
+    // plain stream order (no programmatic launch)
+    void (*jv_tiles)(fe_ctx *c, int precision, const void *v, void *y, int64_t t0, int64_t nt, cudaStream_t st);
+    void (*fix_rows)(fe_ctx *c, int precision, void *y, int64_t r0, int64_t r1, cudaStream_t st);
 };
 
 const OpTable *find_ops(int dim, int d1);
@@ -204,6 +211,11 @@ struct fe_ctx {
     double *w_partial = nullptr;  // reduction partials
     void *h_state = nullptr;      // pinned host mirror
     cudaStream_t own_stream = nullptr;
+    // fe_jacobian_action_host in z-chunks: copy streams, events, the fix-up rows' DOFs on the host
+    bool chunked_host = true;
+    cudaStream_t cp_in = nullptr, cp_out = nullptr;
+    cudaEvent_t chunk_ev[17] = {};
+    std::vector<uint32_t> h_fix_g;
     // captured CG batches: [0] FP64 operator and vectors, [1] FP32 operator with FP64 vectors,
     // [2] FP32 operator and vectors, [3] double-float operator with FP64 vectors
     cudaGraphExec_t cg_exec[4] = { nullptr, nullptr, nullptr, nullptr };

@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<Ti
     constexpr int NTH = TS::THREADS;
     if (P.skip && *P.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t t = blockIdx.x;
+    const int64_t t = P.t0 + blockIdx.x;
     const int tid = threadIdx.x;
     const int64_t tqs = tq_stride<TC>(P);
     const uint32_t tq_bytes = (uint32_t)(tqs * sizeof(TC));
@@ -864,7 +864,7 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     }
     // thread 0 initialises the barrier before it issues the copy; the other threads poll it only
     // after the body's first __syncthreads
-    if (!tile2_body<D1, TT, TIO>(P, Pr, Tq, v, y, halo, blockIdx.x, smem + 64, mbar, 0u, tid, CtaBar{},
+    if (!tile2_body<D1, TT, TIO>(P, Pr, Tq, v, y, halo, P.t0 + blockIdx.x, smem + 64, mbar, 0u, tid, CtaBar{},
                                  AfterPriorGrid{P.skip}) && tid == 0) {
         // the tangent block did not land within the bound: report, let the copy finish
         atomicExch(P.err, 3);
