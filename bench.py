@@ -302,6 +302,10 @@ def run_gpu(args) -> dict | None:
     kres = kernel_ms(res, 10)
     t_res_main = kres.get("residual", float("nan")) / 1e3
     r_host = r.cpu().numpy() if rank == 0 else None
+    # linearisation at the same state: the tangent (FP64 and FP32 copies) and the Jacobi diagonal
+    lin = lambda: op.linearize(u0)
+    tlin, _ = timed(lin, 10, 2)
+    klin = kernel_ms(lin, 5)
     f64peak = fp64_peak()
     live_best, live_med = abi.fe_measure_fp64_peak(10)
 
@@ -427,7 +431,9 @@ def run_gpu(args) -> dict | None:
         "jv_cg_mixed_gdofs": round(nl * ncalls / tcg / 1e9, 4),
         "residual_f64": {"gdofs": round(nl * ncalls / tres / 1e9, 4), "kernel_ms": round(t_res_main * 1e3, 5),
                          "algorithmic_flops": flops_res,
-                         "fp64_frac": round(flops_res / t_res_main / 1e12 / f64peak["tflops"], 4)},
+                         "fp64_frac": round(flops_res / t_res_main / 1e12 / f64peak["tflops"], 4),
+                         "linearize_ms": round(tlin / 10 * 1e3, 5),
+                         "linearize_kernel_ms": {k: round(v, 5) for k, v in klin.items()}},
         "newton": newton,
         "kernel_ms": {"f64": {k: round(v, 5) for k, v in k64.items()},
                       "f32": {k: round(v, 5) for k, v in k32.items()}},

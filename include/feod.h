@@ -87,9 +87,10 @@ typedef struct {
 typedef struct {
     int tile;                  /* elements per tile edge: one CTA owns tile^dim elements;
                                   0 = tuned default                                           */
-    int per_element;           /* 1: apply the cached Jacobian with the per-element kernel
-                                  (element-by-element sum factorisation, staged in-tile G^T)
-                                  instead of the tile-level one (3D); for comparison only     */
+    int per_element;           /* 1: apply the cached Jacobian, and evaluate the residual and
+                                  the tangent, with the per-element kernels (element-by-element
+                                  sum factorisation, staged in-tile G^T) instead of the
+                                  tile-level ones (3D); for comparison only                    */
 } fe_setup_opts;
 
 /* fe_setup: build a context for the mesh, order k (1..6) and quadrature q1d (0 or k+1 Gauss

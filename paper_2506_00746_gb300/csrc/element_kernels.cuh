@@ -986,6 +986,7 @@ __global__ void __launch_bounds__(max_threads(DIM, D1 - 1)) k_vjp(const __grid_c
 
 #include "tma.cuh"
 #include "jv_tile.cuh"
+#include "res_tile.cuh"
 
 namespace feod {
 
@@ -1017,6 +1018,28 @@ struct Ops {
 
     static void residual(fe_ctx *c, const double *u, double *r, double *T64, float *T32, cudaStream_t st)
     {
+        if constexpr (DIM == 3) {
+            if (c->res_tile) {
+                // tile-level collocated kernel (one CTA per tile)
+                constexpr int TT = max_tile(3, D1 - 1);
+                const size_t tsm = res_tile_smem_bytes<D1, TT>();
+                const unsigned grid = (unsigned)c->ntiles;
+                constexpr int NTH = TileShape<D1, TT>::THREADS;
+                const bool tan = T64 || T32;
+                double *halo = reinterpret_cast<double *>(c->d_halo);
+                {
+                    LaunchScope ls(c, r ? "residual" : "linearize", st);
+                    if (r && tan)
+                        k_res_tile<D1, TT, true, true><<<grid, NTH, tsm, st>>>(c->op, c->b64, u, r, halo, T64, T32);
+                    else if (r)
+                        k_res_tile<D1, TT, true, false><<<grid, NTH, tsm, st>>>(c->op, c->b64, u, r, halo, T64, T32);
+                    else if (tan)
+                        k_res_tile<D1, TT, false, true><<<grid, NTH, tsm, st>>>(c->op, c->b64, u, r, halo, T64, T32);
+                }
+                if (r) fixup<double, double>(c, r, st);
+                return;
+            }
+        }
         const size_t sm = smem_bytes<DIM, D1>(c->S, c->T, sizeof(double), 1);
         {
             LaunchScope ls(c, r ? "residual" : "linearize", st);
@@ -1118,6 +1141,36 @@ struct Ops {
         }
         return cudaSuccess;
     }
+    // Enable the tile-level residual / tangent kernel (3D, the compiled tile edge, not the
+    // per-element comparison mode) when its three variants fit; otherwise k_residual runs.
+    static cudaError_t prepare_res_tile(fe_ctx *c)
+    {
+        c->res_tile = false;
+        if constexpr (DIM == 3) {
+            constexpr int TT = max_tile(3, D1 - 1);
+            constexpr int NTH = TileShape<D1, TT>::THREADS;
+            if (c->per_element || c->T != TT || c->ntiles > 0x7fffffff) return cudaSuccess;
+            const size_t tsm = res_tile_smem_bytes<D1, TT>();
+            if (tsm > (size_t)c->smem_optin) return cudaSuccess;
+            const void *kerns[3] = { reinterpret_cast<const void *>(k_res_tile<D1, TT, true, true>),
+                                     reinterpret_cast<const void *>(k_res_tile<D1, TT, true, false>),
+                                     reinterpret_cast<const void *>(k_res_tile<D1, TT, false, true>) };
+            for (const void *kern : kerns) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+                if (e != cudaSuccess) return e;
+                cudaFuncAttributes fa;
+                if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+                if (fa.maxThreadsPerBlock < NTH) return cudaSuccess;
+                int per_sm = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTH, tsm);
+                if (e != cudaSuccess) return e;
+                if (per_sm < 1) return cudaSuccess;
+            }
+            c->res_tile = true;
+        }
+        return cudaSuccess;
+    }
+
     // the tile kernel alone on tiles [t0, t0 + nt) (3D, tile kernel enabled; plain launch)
     template <typename TC, typename TIO>
     static void jv_tile_range(fe_ctx *c, const TIO *v, TIO *y, int64_t t0, int64_t nt, cudaStream_t st)
@@ -1238,6 +1291,7 @@ struct Ops {
         FEOD_RAISE((k_vjp<DIM, D1>), s2d);
 #undef FEOD_RAISE
         if (e != cudaSuccess) return e;
+        if ((e = prepare_res_tile(c)) != cudaSuccess) return e;
         if ((e = prepare_tile<double, double>(c)) != cudaSuccess) return e;
         if ((e = prepare_tile<float, float>(c)) != cudaSuccess) return e;
         if ((e = prepare_tile<float, double>(c)) != cudaSuccess) return e;

@@ -171,6 +171,7 @@ struct fe_ctx {
     // FP64 vectors, double-float with FP64 vectors]; 0 = that variant runs the per-element kernel
     int pipe_grid[4] = { 0, 0, 0, 0 };
     bool per_element = false;       // the cached J v uses the per-element kernel (comparison)
+    bool res_tile = false;          // R(u) and the tangent run the tile-level kernel (3D)
     int smem_optin = 0;
     int *h_err = nullptr;                       // pinned mirror of d_err
     int NQ = 0, NS = 0, NG = 0;                 // points per element, sym entries, geo comps

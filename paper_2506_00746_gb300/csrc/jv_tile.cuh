@@ -240,6 +240,15 @@ struct Colloc {
     __host__ __device__ static void x3(const BasisT<TC> &Bs, const TC *fx, const TC *FY, const TC *FZ, TC *C,
                                        TC *SX, int tid)
     {
+        x3s<TC, false>(Bs, fx, fx, FY, FZ, C, SX, tid);
+    }
+
+    // x3 with (HAS_S) a value term s at this thread's Q1 points: W = Dc^T F + s before B_x^T (the
+    // residual's load term); without it the sums start from zero
+    template <typename TC, bool HAS_S>
+    __host__ __device__ static void x3s(const BasisT<TC> &Bs, const TC *fx, const TC *s, const TC *FY,
+                                        const TC *FZ, TC *C, TC *SX, int tid)
+    {
         const int L = tid % NLP, h = tid / NLP;
         if (L >= QT * QT) return;
         const int qz = L % QT, qy = L / QT;
@@ -248,7 +257,7 @@ struct Colloc {
         // the Q1 sums W[q] (each over j ascending, x then y then z term) advance together
         TC w[Q1];
 #pragma unroll
-        for (int q = 0; q < Q1; ++q) w[q] = TC(0);
+        for (int q = 0; q < Q1; ++q) w[q] = HAS_S ? s[q] : TC(0);
 #pragma unroll
         for (int j = 0; j < Q1; ++j)
 #pragma unroll

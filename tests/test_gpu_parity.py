@@ -136,6 +136,45 @@ def test_tile_and_per_element_jacobian_kernels(n, k):
     assert _rel(outs[0][1], outs[1][1]) <= 1e-6
 
 
+@pytest.mark.parametrize("n,k,p,eps,rho", [(7, 1, 3.0, 0.0, False), (5, 2, 2.5, 0.0, True), (5, 3, 3.0, 0.0, False),
+                                           (3, 3, 1.5, 0.5, True), (4, 4, 4.0, 0.0, False), (3, 5, 3.7, 1e-3, False),
+                                           (2, 6, 3.0, 0.0, True)])
+def test_tile_and_per_element_residual_kernels(n, k, p, eps, rho):
+    """The tile-level residual / tangent kernel (collocated stages, flux and dual tangent at each
+    point) and the per-element one both match the oracle: R(u) alone, the tangent alone (through
+    the cached FP64 and FP32 J v), and R with the tangent in one pass (Newton's fused call, through
+    the FP32 J v it leaves cached).  Ragged last tiles (n not a multiple of the tile edge), the
+    design factor and the generic power law are covered."""
+    import torch
+    from paper_2506_00746_gb300 import Operator
+    V = I.lattice_vertices(3, n, seed=0)
+    r = I.design_field(3, n, seed=3) if rho else None
+    P = O.Problem(3, n, k, V, p=p, eps=eps, rho=r)
+    u = I.smooth_field(3, n, k, seed=1)
+    v = I.uniform_vector(P.n_dofs, seed=2)
+    ud, vd = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
+    r_ref, y_ref = O.residual(P, u), O.jv(P, u, v)
+    y_ref32 = O.jv(P, u, vd.float().double().cpu().numpy())
+    outs = []
+    for tile_kernel in (True, False):
+        op = Operator(3, n, k, V, p=p, eps=eps, rho=r, tile_kernel=tile_kernel)
+        res = op.residual(ud).cpu().numpy()
+        assert _rel(res, r_ref) <= TOL64
+        op.linearize(ud)
+        y64 = op.jacobian_action(vd, precision=64).cpu().numpy()
+        assert _rel(y64, y_ref) <= TOL64
+        assert _rel(op.jacobian_action(vd.float(), precision=32).double().cpu().numpy(), y_ref32) <= TOL32
+        # the fused residual + FP32 tangent of the mixed Newton step: one Newton step from u runs
+        # it at u first; its reported initial residual norm is ||R(u)||
+        w = ud.clone()
+        rep = op.newton_solve(w, rtol=1e-30, max_newton=1, inner_precision=32, raise_on_error=False)
+        assert abs(rep["r0"] - np.linalg.norm(r_ref)) <= 1e-12 * np.linalg.norm(r_ref)
+        outs.append((res, y64))
+        op.close()
+    assert _rel(outs[0][0], outs[1][0]) <= 1e-13
+    assert _rel(outs[0][1], outs[1][1]) <= 1e-13
+
+
 def test_bitwise_reproducible():
     import torch
     op, P, u, v, ud, vd = _case(3, 6, 3)
