@@ -179,7 +179,7 @@ def kernel_source_hash() -> str:
     parameter blocks of internal.h (the host context that follows them does not enter)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2506_00746_gb300", "csrc")
-    for f in ("element_kernels.cuh", "jv_tile.cuh", "tma.cuh"):
+    for f in ("element_kernels.cuh", "jv_tile.cuh", "res_tile.cuh", "tma.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     internal = open(os.path.join(csrc, "internal.h"), "rb").read()
     h.update(internal.split(b"// The context.")[0])
@@ -949,6 +949,26 @@ def run_jv_small(args) -> dict:
     return out
 
 
+def run_residual_small(args) -> dict:
+    """`reps` FP64 residual evaluations R(u) of one 3D p=3 instance at the seeded smooth state (the
+    small case of the residual-kernel captures)."""
+    import torch
+
+    from paper_2506_00746_gb300 import Operator
+    from paper_2506_00746_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    V = I.lattice_vertices(3, args.n, seed=0)
+    op = Operator(3, args.n, args.order, V, p=3.0)
+    u = torch.from_numpy(I.smooth_field(3, args.n, args.order, seed=1)).cuda()
+    for _ in range(args.reps):
+        r = op.residual(u)
+    torch.cuda.synchronize()
+    out = {"suite": "residual", "n": args.n, "order": args.order, "reps": args.reps, "n_dofs": op.n_dofs,
+           "norm": float(r.norm())}
+    op.close()
+    return out
+
+
 def run_cg_small(args) -> dict:
     """`reps` Jacobi-preconditioned CG iterations (fe_cg_solve, precision as given) on one 3D p=3
     instance linearised at the seeded smooth state, with the load vector as right-hand side and an
@@ -1135,11 +1155,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--max-newton", type=int, default=50)
-    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "element-ad", "jv", "batch-subset",
+    ap.add_argument("--suite", choices=["headline", "sweep", "design", "batched", "element-ad", "jv", "residual",
+                                        "batch-subset",
                                         "fp64-peak", "cg"],
                     default="headline",
                     help="headline (the benchmark line), sweep (orders 1-6), design (adjoint case), batched "
-                         "(64 instances in one persistent launch); jv and batch-subset run the small cases "
+                         "(64 instances in one persistent launch); jv, residual and batch-subset run the small cases "
                          "of the ncu captures")
     ap.add_argument("--n", type=int, default=48)
     ap.add_argument("--order", type=int, default=3)
@@ -1159,7 +1180,7 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.suite != "headline" and args.impl == "gpu":
         out = {"sweep": run_sweep, "design": run_design, "batched": run_batched, "element-ad": run_element_ad,
-               "jv": run_jv_small, "fp64-peak": run_fp64_peak, "cg": run_cg_small,
+               "jv": run_jv_small, "residual": run_residual_small, "fp64-peak": run_fp64_peak, "cg": run_cg_small,
                "batch-subset": run_batch_subset}[args.suite](args)
     elif args.impl == "reference":
         out = run_reference(args)
