@@ -381,6 +381,7 @@ def run_gpu(args) -> dict | None:
     traffic32, traffic32_src = profiled_traffic(k32name)
     traffic_fix32, _ = profiled_traffic("k_fixup<float,float>")
     flops_res = residual_algorithmic_flops(w.dim, ne, w.order + 1, w.order + 1)
+    traffic_res, traffic_res_src = profiled_traffic("k_res_tile<4,2,1,0>")
     out = {
         "metric": METRIC,
         "value": round(value, 4),
@@ -432,6 +433,7 @@ def run_gpu(args) -> dict | None:
         "residual_f64": {"gdofs": round(nl * ncalls / tres / 1e9, 4), "kernel_ms": round(t_res_main * 1e3, 5),
                          "algorithmic_flops": flops_res,
                          "fp64_frac": round(flops_res / t_res_main / 1e12 / f64peak["tflops"], 4),
+                         "traffic": traffic_res, "traffic_summary": traffic_res_src,
                          "linearize_ms": round(tlin / 10 * 1e3, 5),
                          "linearize_kernel_ms": {k: round(v, 5) for k, v in klin.items()}},
         "newton": newton,

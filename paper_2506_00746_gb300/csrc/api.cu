@@ -230,6 +230,9 @@ fe_status apply_jv_cached(fe_ctx *c, const void *v, void *y, int precision, cuda
     return FE_OK;
 }
 
+// the precision -32 CG feeds its FP32 operator an FP32 copy of the direction (tile kernel only)
+bool cg_shadow(const fe_ctx *c) { return c->cg_shadow && c->ops->jv_pa_32s != nullptr; }
+
 // Enqueue `m` CG iterations (J p, alpha, update, direction); every kernel is a no-op once the
 // device flag `done` is set.  precision 64: FP64 operator and vectors; 48: double-float operator,
 // FP64 vectors; -32: FP32 operator, FP64 vectors; 32: FP32 operator and vectors (CG scalars and
@@ -242,12 +245,16 @@ void enqueue_cg(fe_ctx *c, int m, int precision, cudaStream_t st)
     c->fix.skip = &s->done;
     for (int i = 0; i < m; ++i) {
         if (precision != 32) {
+            // precision -32 with the tile kernel: the operator reads the FP32 copy of p that the
+            // direction kernel writes (the conversion moves out of the operator's gather)
+            float *p32 = precision == -32 && cg_shadow(c) ? c->w_fp : nullptr;
             if (precision == 64) c->ops->jv_pa_64(c, c->w_cp, c->w_cq, st);
             else if (precision == 48) c->ops->jv_pa_df(c, c->w_cp, c->w_cq, st);
-            else c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
+            else if (!p32) c->ops->jv_pa_32d(c, c->w_cp, c->w_cq, st);
+            else c->ops->jv_pa_32s(c, p32, c->w_cp, c->w_cq, st);
             { LaunchScope ls(c, "cg_alpha", st); k_cg_alpha<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cp, c->w_cq, n, s, c->w_partial); }
             { LaunchScope ls(c, "cg_update", st); k_cg_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cr, c->w_cq, c->w_dinv64, c->w_cz, n, s, c->w_partial); }
-            { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cx, c->w_cp, c->w_cz, n, s); }
+            { LaunchScope ls(c, "cg_direction", st); k_cg_direction<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cx, c->w_cp, p32, c->w_cz, c->w_cr, n, s, c->w_partial); }
         } else {
             c->ops->jv_pa_32(c, c->w_fp, c->w_fq, st);
             { LaunchScope ls(c, "cg_alpha32", st); k_cg_alpha32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_fp, c->w_fq, n, s, c->w_partial); }
@@ -294,12 +301,13 @@ fe_status run_cg(fe_ctx *c, const double *b, double rtol, int max_iter, int prec
             k_scale_rhs<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(c->w_cq, b, c->nl, &ds->scalar, s);
         }
         LaunchScope ls(c, "cg_init", st);
-        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cq, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, c->nl, s,
-                                                      rtol, max_iter, c->w_partial);
+        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(c->w_cq, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, nullptr,
+                                                      c->nl, s, rtol, max_iter, c->w_partial);
     } else if (precision != 32) {
         LaunchScope ls(c, "cg_init", st);
-        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp, c->nl, s, rtol,
-                                                      max_iter, c->w_partial);
+        k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, c->w_dinv64, c->w_cx, c->w_cr, c->w_cp,
+                                                      precision == -32 && cg_shadow(c) ? c->w_fp : nullptr, c->nl,
+                                                      s, rtol, max_iter, c->w_partial);
     } else {
         CgState *ds = s + 1;
         {

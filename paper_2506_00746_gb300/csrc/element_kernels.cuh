@@ -1081,7 +1081,7 @@ struct Ops {
                         cfg.numAttrs = (c->capturing || c->prof) ? 0 : 1;
                         cudaLaunchKernelEx(&cfg, k_jv_tile2<D1, TT, TIO>, c->op, c->p32,
                                            reinterpret_cast<const float *>(Tq), v, y,
-                                           reinterpret_cast<float *>(c->d_halo));
+                                           reinterpret_cast<float *>(c->d_halo), (const TIO *)nullptr);
                     } else {
                         const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
                         k_jv_tile<D1, TT, TC, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(
@@ -1141,6 +1141,30 @@ struct Ops {
         }
         return cudaSuccess;
     }
+    // The CG's FP32 operator on the FP32 rounding of its FP64 direction (FP32 input, FP64 output):
+    // the same shape as the FP32 variant.
+    static cudaError_t prepare_cg_shadow(fe_ctx *c)
+    {
+        c->cg_shadow = false;
+        if constexpr (DIM == 3) {
+            constexpr int TT = max_tile(3, D1 - 1);
+            constexpr int NTH = TileShape<D1, TT>::THREADS;
+            if (c->pipe_grid[2] == 0) return cudaSuccess;
+            const void *kern = reinterpret_cast<const void *>(k_jv_tile2<D1, TT, float, double>);
+            const size_t tsm = tile2_smem_bytes<D1, TT, float>(c->tqs32);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+            if (e != cudaSuccess) return e;
+            cudaFuncAttributes fa;
+            if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+            if (fa.maxThreadsPerBlock < NTH) return cudaSuccess;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTH, tsm);
+            if (e != cudaSuccess) return e;
+            c->cg_shadow = per_sm >= 1;
+        }
+        return cudaSuccess;
+    }
+
     // Enable the tile-level residual / tangent kernel (3D, the compiled tile edge, not the
     // per-element comparison mode) when its three variants fit; otherwise k_residual runs.
     static cudaError_t prepare_res_tile(fe_ctx *c)
@@ -1194,7 +1218,7 @@ struct Ops {
                 LaunchScope ls(c, "jv_pa_f32", st);
                 const size_t tsm = tile2_smem_bytes<D1, TT, TIO>(c->tqs32);
                 k_jv_tile2<D1, TT, TIO><<<(unsigned)nt, TileShape<D1, TT>::THREADS, tsm, st>>>(
-                    P, c->p32, c->d_T32, v, y, reinterpret_cast<float *>(c->d_halo));
+                    P, c->p32, c->d_T32, v, y, reinterpret_cast<float *>(c->d_halo), (const TIO *)nullptr);
             }
         }
     }
@@ -1211,6 +1235,37 @@ struct Ops {
         else if (precision == 48) fixup<dfloat, double>(c, (double *)y, st, r0, r1);
         else if (precision == -32) fixup<float, double>(c, (double *)y, st, r0, r1);
         else fixup<float, float>(c, (float *)y, st, r0, r1);
+    }
+    // The CG's FP32 operator with FP64 vectors from the FP32 rounding of the direction: q = J p
+    // (FP64 output) from p32 = fl32(p), essential rows copied from p; bit for bit jv_pa_32d on p.
+    // False, with nothing launched, where the tile kernel does not run.
+    static bool jv_pa_32s(fe_ctx *c, const float *p32, const double *p, double *q, cudaStream_t st)
+    {
+        if constexpr (DIM == 3) {
+            if (!c->cg_shadow || c->pipe_grid[2] == 0) return false;
+            constexpr int TT = max_tile(3, D1 - 1);
+            {
+                LaunchScope ls(c, "jv_pa_f32", st);
+                // programmatic launch as jv_pa's, except in the library's own graphs and under
+                // per-kernel timing
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                at[0].val.programmaticStreamSerializationAllowed = 1;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)c->pipe_grid[2]);
+                cfg.blockDim = dim3(TileShape<D1, TT>::THREADS);
+                cfg.dynamicSmemBytes = tile2_smem_bytes<D1, TT, float>(c->tqs32);
+                cfg.stream = st;
+                cfg.attrs = at;
+                cfg.numAttrs = (c->capturing || c->prof) ? 0 : 1;
+                cudaLaunchKernelEx(&cfg, k_jv_tile2<D1, TT, float, double>, c->op, c->p32,
+                                   reinterpret_cast<const float *>(c->d_T32), p32, q,
+                                   reinterpret_cast<float *>(c->d_halo), p);
+            }
+            fixup<float, double>(c, q, st);
+            return true;
+        }
+        return false;
     }
     static void jv_pa_64(fe_ctx *c, const double *v, double *y, cudaStream_t st) { jv_pa<double, double>(c, v, y, st); }
     static void jv_pa_32(fe_ctx *c, const float *v, float *y, cudaStream_t st) { jv_pa<float, float>(c, v, y, st); }
@@ -1299,6 +1354,7 @@ struct Ops {
         // the two FP32 variants must run the same kernel (the FP64-vector one is defined to give
         // exactly the FP32 result): use the tile kernel for both or for neither
         if (c->pipe_grid[1] == 0 || c->pipe_grid[2] == 0) c->pipe_grid[1] = c->pipe_grid[2] = 0;
+        if ((e = prepare_cg_shadow(c)) != cudaSuccess) return e;
         return cudaSuccess;
     }
 
@@ -1306,7 +1362,7 @@ struct Ops {
     {
         static const OpTable t = { DIM, D1, residual, jv_pa_64, jv_pa_32, jv_pa_32d, jv_pa_df,
                                    jv_dual_64, jv_dual_32, jv_dual_32d, diag_64, diag_32, vjp,
-                                   prepare, max_smem, jv_tiles, fix_rows };
+                                   prepare, max_smem, jv_tiles, fix_rows, jv_pa_32s };
         return &t;
     }
 };

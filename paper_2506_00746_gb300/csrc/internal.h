@@ -151,6 +151,10 @@ struct OpTable {
     // plain stream order (no programmatic launch)
     void (*jv_tiles)(fe_ctx *c, int precision, const void *v, void *y, int64_t t0, int64_t nt, cudaStream_t st);
     void (*fix_rows)(fe_ctx *c, int precision, void *y, int64_t r0, int64_t r1, cudaStream_t st);
+    // the CG's FP32 operator with FP64 vectors (precision -32) fed by the FP32 rounding p32 of the
+    // direction p (the CG direction kernel writes both): q = J p in FP64, bit for bit jv_pa_32d on
+    // p; false, with nothing launched, where the tile kernel does not run
+    bool (*jv_pa_32s)(fe_ctx *c, const float *p32, const double *p, double *q, cudaStream_t st);
 };
 
 const OpTable *find_ops(int dim, int d1);
@@ -172,6 +176,7 @@ struct fe_ctx {
     int pipe_grid[4] = { 0, 0, 0, 0 };
     bool per_element = false;       // the cached J v uses the per-element kernel (comparison)
     bool res_tile = false;          // R(u) and the tangent run the tile-level kernel (3D)
+    bool cg_shadow = false;         // the precision -32 CG feeds its operator an FP32 copy of p
     int smem_optin = 0;
     int *h_err = nullptr;                       // pinned mirror of d_err
     int NQ = 0, NS = 0, NG = 0;                 // points per element, sym entries, geo comps

@@ -21,6 +21,8 @@
 // tangent block into shared memory while the threads gather the DOF block.
 #pragma once
 
+#include <type_traits>
+
 namespace feod {
 
 __host__ __device__ constexpr inline size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -552,12 +554,14 @@ struct GroupBar {
 // prologue loaded into registers (shared-memory codes only; their latency overlaps the z stage).
 // tangent_ready() runs in every thread before the x stage (the first reader of Tb) and returns
 // false, uniformly, to abandon the tile.
-template <int D1, int TT, typename TIO, typename Bar, typename StoreHd, typename Ready>
+// vess: the source of the essential rows' output (J v = v there), v itself unless the output type
+// differs from the input type.
+template <int D1, int TT, typename TIO, typename TOUT, typename Bar, typename StoreHd, typename Ready>
 __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *Tb, const TIO *Vs,
                                              const uint32_t *__restrict__ codes, const uint32_t *__restrict__ hd,
                                              float2 *A2, float *C1,
                                              float2 *C2, float *SX1, float2 *SX2, float2 *SY2, float *SZ1,
-                                             const TIO *__restrict__ v, TIO *__restrict__ y,
+                                             const TOUT *__restrict__ vess, TOUT *__restrict__ y,
                                              float *__restrict__ halo, int tid, const Bar &bar,
                                              StoreHd store_hd, Ready tangent_ready)
 {
@@ -716,9 +720,9 @@ __device__ __forceinline__ bool tile_stages2(const BasisPairs &Pr, const float *
         if (code & SLOT_HALO) {
             if (!(code & SLOT_ESS)) halo[TS::LATE_CODES ? zh[a] : hd[s]] = val;
         } else if (code & SLOT_ESS) {
-            y[g] = v[g];
+            y[g] = vess[g];
         } else {
-            y[g] = (TIO)val;
+            y[g] = (TOUT)val;
         }
     };
     if (actz) {
@@ -775,12 +779,14 @@ struct AfterPriorGrid {
 // the caller then reports and waits for it again.  The slot codes (set-up data) are requested
 // first: the input values depend on them, and they are the longest chain of a tile's prologue;
 // the tangent copy (waited for only before the x stage) is issued after them.
-template <int D1, int TT, typename TIO, typename Bar, typename Ready = InputsReady>
+// TOUT: the output type (TIO unless given); vess: the essential rows' source when TOUT differs
+// from TIO (v itself otherwise).
+template <int D1, int TT, typename TIO, typename Bar, typename Ready = InputsReady, typename TOUT = TIO>
 __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &Pr, const float *__restrict__ Tq,
-                                           const TIO *__restrict__ v, TIO *__restrict__ y,
+                                           const TIO *__restrict__ v, TOUT *__restrict__ y,
                                            float *__restrict__ halo, int64_t t, unsigned char *smem,
                                            uint64_t *mbar, uint32_t parity, int tid, const Bar &bar,
-                                           Ready inputs_ready = Ready{})
+                                           Ready inputs_ready = Ready{}, const TOUT *vess = nullptr)
 {
     using TS = TileShape2<D1, TT>;
     constexpr int NS3 = TS::NS3, NTH = TS::THREADS;
@@ -839,8 +845,11 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
     // makes the gathered block (and, in a new CTA, the mbarrier initialisation) visible to all
     // threads; the tangent block is waited for (bounded) only before the x stage, its first reader
     bar.sync();
+    const TOUT *ess;
+    if constexpr (std::is_same<TIO, TOUT>::value) ess = vess ? vess : v;
+    else ess = vess;
     return tile_stages2<D1, TT, TIO>(
-        Pr, Tb, Vs, TS::LATE_CODES ? sl : codes, TS::LATE_CODES ? hs : hd, A2, C1, C2, SX1, SX2, SY2, SZ1, v, y,
+        Pr, Tb, Vs, TS::LATE_CODES ? sl : codes, TS::LATE_CODES ? hs : hd, A2, C1, C2, SX1, SX2, SY2, SZ1, ess, y,
         halo, tid, bar,
         [&]() {
             if constexpr (!TS::LATE_CODES) {
@@ -858,11 +867,15 @@ __device__ __forceinline__ bool tile2_body(const OpParams &P, const BasisPairs &
 // programmatically after the fix-up of the previous action (outside graph captures): the CTAs
 // of its first wave initialise their mbarrier and request their slot codes (set-up data) while
 // that fix-up ends, then wait for it before they touch anything a kernel before them wrote.
-template <int D1, int TT, typename TIO>
+// TOUT (default TIO): the output type; the CG with FP64 vectors feeds the FP32 rounding of its
+// direction (TIO float) and takes an FP64 output, its essential rows copied from vess (the FP64
+// direction), so that the result is bit for bit the one of the FP64-input variant on that
+// direction.
+template <int D1, int TT, typename TIO, typename TOUT = TIO>
 __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     k_jv_tile2(const __grid_constant__ OpParams P, const __grid_constant__ BasisPairs Pr,
-               const float *__restrict__ Tq, const TIO *__restrict__ v, TIO *__restrict__ y,
-               float *__restrict__ halo)
+               const float *__restrict__ Tq, const TIO *__restrict__ v, TOUT *__restrict__ y,
+               float *__restrict__ halo, const TOUT *__restrict__ vess)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
@@ -873,8 +886,9 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::THREADS)
     }
     // thread 0 initialises the barrier before it issues the copy; the other threads poll it only
     // after the body's first __syncthreads
-    if (!tile2_body<D1, TT, TIO>(P, Pr, Tq, v, y, halo, P.t0 + blockIdx.x, smem + 64, mbar, 0u, tid, CtaBar{},
-                                 AfterPriorGrid{P.skip}) && tid == 0) {
+    if (!tile2_body<D1, TT, TIO, CtaBar, AfterPriorGrid, TOUT>(P, Pr, Tq, v, y, halo, P.t0 + blockIdx.x, smem + 64,
+                                                               mbar, 0u, tid, CtaBar{}, AfterPriorGrid{P.skip},
+                                                               vess) && tid == 0) {
         // the tangent block did not land within the bound: report, let the copy finish
         atomicExch(P.err, 3);
         mbar_wait_bounded(mbar, 0);

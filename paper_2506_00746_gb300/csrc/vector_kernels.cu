@@ -238,16 +238,18 @@ __global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b
     if (last_block_sum<1>(s, partial, counter, r, sh) && threadIdx.x == 0) *out = r[0];
 }
 
-// CG start (x = 0): r = b, p = z = dinv b; rz = r.z, rr = r.r; tol2 = rtol^2 rr.
+// CG start (x = 0): r = b, p = z = dinv b (and its FP32 rounding p32 unless null); rz = r.z,
+// rr = r.r; tol2 = rtol^2 rr.
 __global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, double *__restrict__ x,
-                          double *__restrict__ r, double *__restrict__ p, int64_t n, CgState *st, double rtol,
-                          int max_iter, double *partial)
+                          double *__restrict__ r, double *__restrict__ p, float *__restrict__ p32, int64_t n,
+                          CgState *st, double rtol, int max_iter, double *partial)
 {
     __shared__ double sh[RED_THREADS];
     double s[2] = { 0.0, 0.0 };
     for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
         const double bi = b[i], zi = dinv[i] * bi;
         x[i] = 0.0; r[i] = bi; p[i] = zi;
+        if (p32) p32[i] = (float)zi;
         s[0] += bi * zi; s[1] += bi * bi;
     }
     double o[2];
@@ -289,16 +291,18 @@ __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restric
     }
 }
 
-// r -= alpha q; z = dinv r (stored); rz' = r.z, rr = r.r; beta = rz'/rz; convergence test.  The
-// matching update of x (x += alpha p) is left to k_cg_direction, which reads p anyway: xpend says
-// it is due, also in the iteration that converges.
+// r -= alpha q; z = dinv r (stored); rz' = r.z; beta = rz'/rz.  The rest of the iteration is
+// k_cg_direction's: the update of x (x += alpha p, xpend says it is due), the new direction, and
+// the convergence test with r.r (the inner product that only the test needs).  This kernel thus
+// does three FP64 operations per DOF (GB300's FP64 unit bounds it) and the direction kernel,
+// which is bound by HBM, takes the fourth.
 __global__ void k_cg_update(double *__restrict__ r, const double *__restrict__ q, const double *__restrict__ dinv,
                             double *__restrict__ z, int64_t n, CgState *st, double *partial)
 {
     if (st->done) return;
     __shared__ double sh[RED_THREADS];
     const double alpha = st->alpha;
-    double s[2] = { 0.0, 0.0 };
+    double s[1] = { 0.0 };
     const int64_t gs = (int64_t)gridDim.x * RED_THREADS;
     for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += BATCH * gs) {
         double rv[BATCH], qv[BATCH], dv[BATCH];
@@ -315,47 +319,59 @@ __global__ void k_cg_update(double *__restrict__ r, const double *__restrict__ q
                 const double zi = dv[u] * ri;
                 r[j] = ri;
                 z[j] = zi;
-                s[0] += ri * zi; s[1] += ri * ri;
+                s[0] += ri * zi;
             }
         }
     }
-    double o[2];
-    if (last_block_sum<2>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+    double o[1];
+    if (last_block_sum<1>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
         st->beta = o[0] / st->rz;
-        st->rz = o[0]; st->rr = o[1];
+        st->rz = o[0];
         st->iter += 1;
         st->xpend = 1;
-        if (!isfinite(o[1])) st->done = CG_NAN;
-        else if (o[1] <= st->tol2) st->done = CG_CONVERGED;
-        else if (st->iter >= st->max_iter) st->done = CG_MAXIT;
     }
 }
 
-// x += alpha p (the update of the last k_cg_update, when xpend says it is due), then, unless the
-// CG has stopped, p = z + beta p.  The last block (by ticket) clears xpend: every block has read it
-// before it takes its ticket.
+// x += alpha p (the update of the last k_cg_update, when xpend says it is due); unless the CG has
+// stopped: p = z + beta p (and p's FP32 rounding p32 unless null, the input of the FP32 operator),
+// rr = r.r summed over the thread grid and order that k_cg_update uses, and the convergence test
+// of that iteration (done when rr <= tol2, not finite, or at max_iter).  In the iteration that
+// converges p is updated although no later iteration reads it.  The last block (by ticket) sets
+// the flags and clears xpend: every block has read it before it takes its ticket.
 __global__ void __launch_bounds__(VEC_THREADS, 4) k_cg_direction(double *__restrict__ x, double *__restrict__ p,
-                                                                  const double *__restrict__ z, int64_t n,
-                                                                  CgState *st)
+                                                                  float *__restrict__ p32,
+                                                                  const double *__restrict__ z,
+                                                                  const double *__restrict__ r, int64_t n,
+                                                                  CgState *st, double *partial)
 {
+    static_assert(VEC_THREADS == RED_THREADS && VEC_BLOCKS == RED_BLOCKS, "rr uses k_cg_update's grid");
     if (!st->xpend) return;
+    __shared__ double sh[RED_THREADS];
     const double alpha = st->alpha, beta = st->beta;
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
-    if (st->done == 0) {
+    const bool running = st->done == 0;
+    double s[1] = { 0.0 };
+    // two of the thread's elements per round (four arrays read): the loads in flight cover the
+    // latency at 64 registers without spills; the sum's order is the plain loop's either way
+    constexpr int DB = 2;
+    if (running) {
 #pragma unroll 1
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += BATCH * gs) {
-            double xv[BATCH], pv[BATCH], zv[BATCH];
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += DB * gs) {
+            double xv[DB], pv[DB], zv[DB], rv[DB];
 #pragma unroll
-            for (int u = 0; u < BATCH; ++u) {
+            for (int u = 0; u < DB; ++u) {
                 const int64_t j = i + u * gs;
-                if (j < n) { xv[u] = x[j]; pv[u] = p[j]; zv[u] = z[j]; }
+                if (j < n) { xv[u] = x[j]; pv[u] = p[j]; zv[u] = z[j]; rv[u] = r[j]; }
             }
 #pragma unroll
-            for (int u = 0; u < BATCH; ++u) {
+            for (int u = 0; u < DB; ++u) {
                 const int64_t j = i + u * gs;
                 if (j < n) {
                     x[j] = xv[u] + alpha * pv[u];
-                    p[j] = zv[u] + beta * pv[u];
+                    const double pn = zv[u] + beta * pv[u];
+                    p[j] = pn;
+                    if (p32) p32[j] = (float)pn;
+                    s[0] += rv[u] * rv[u];
                 }
             }
         }
@@ -363,13 +379,15 @@ __global__ void __launch_bounds__(VEC_THREADS, 4) k_cg_direction(double *__restr
         // the CG has stopped: only the last iteration's x update remains
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) x[i] = x[i] + alpha * p[i];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(&st->counter, 1u);
-        if (ticket == gridDim.x - 1) {
-            st->xpend = 0;
-            st->counter = 0u;
+    double o[1];
+    if (last_block_sum<1>(s, partial, &st->counter, o, sh) && threadIdx.x == 0) {
+        if (running) {
+            st->rr = o[0];
+            if (!isfinite(o[0])) st->done = CG_NAN;
+            else if (o[0] <= st->tol2) st->done = CG_CONVERGED;
+            else if (st->iter >= st->max_iter) st->done = CG_MAXIT;
         }
+        st->xpend = 0;
     }
 }
 

@@ -42,14 +42,15 @@ __global__ void k_design_factors(const GeomParams G, const double *__restrict__ 
 __global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *partial,
                       unsigned *counter, double *out);
 __global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, double *__restrict__ x,
-                          double *__restrict__ r, double *__restrict__ p, int64_t n, CgState *st, double rtol,
-                          int max_iter, double *partial);
+                          double *__restrict__ r, double *__restrict__ p, float *__restrict__ p32, int64_t n,
+                          CgState *st, double rtol, int max_iter, double *partial);
 __global__ void k_cg_alpha(const double *__restrict__ p, const double *__restrict__ q, int64_t n, CgState *st,
                            double *partial);
 __global__ void k_cg_update(double *__restrict__ r, const double *__restrict__ q, const double *__restrict__ dinv,
                             double *__restrict__ z, int64_t n, CgState *st, double *partial);
-__global__ void k_cg_direction(double *__restrict__ x, double *__restrict__ p, const double *__restrict__ z,
-                               int64_t n, CgState *st);
+__global__ void k_cg_direction(double *__restrict__ x, double *__restrict__ p, float *__restrict__ p32,
+                               const double *__restrict__ z, const double *__restrict__ r, int64_t n,
+                               CgState *st, double *partial);
 __global__ void k_waxpy(double *__restrict__ y, const double *__restrict__ a, double alpha,
                         const double *__restrict__ b, int64_t n);
 __global__ void k_scale(double *__restrict__ y, const double *__restrict__ x, double alpha, int64_t n);
