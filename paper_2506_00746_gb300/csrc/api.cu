@@ -744,7 +744,11 @@ extern "C" void fe_destroy(fe_ctx *c)
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->cp_in) cudaStreamDestroy(c->cp_in);
     if (c->cp_out) cudaStreamDestroy(c->cp_out);
+    for (cudaStream_t t : c->cp_tile)
+        if (t) cudaStreamDestroy(t);
     for (cudaEvent_t e : c->chunk_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tile_ev)
         if (e) cudaEventDestroy(e);
     for (auto &g : c->cg_loop_exec)
         if (g) cudaGraphExecDestroy(g);
@@ -868,7 +872,9 @@ fe_status jv_host_chunked(fe_ctx *c, const void *v_host, void *y_host, int preci
     if (!c->cp_in) {
         CK(cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking));
+        for (auto &t : c->cp_tile) CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
         for (auto &e : c->chunk_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto &e : c->tile_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     // the rows of each length class (1, 3, 7 halo entries), sorted by DOF within the class
     const int64_t cls0[3] = { 0, c->fix.n1, c->fix.n1 + c->fix.n3 };
@@ -893,9 +899,16 @@ fe_status jv_host_chunked(fe_ctx *c, const void *v_host, void *y_host, int preci
             in_end = need;
         }
         CK(cudaEventRecord(ein, c->cp_in));
-        CK(cudaStreamWaitEvent(st, ein, 0));
-        c->ops->jv_tiles(c, precision, dv, dy, L0 * ntxy, (L1 - L0) * ntxy, st);
+        // the chunks' tile kernels alternate between two streams, so that one chunk's last wave
+        // of tiles runs beside the next chunk's first: they write disjoint owned rows and halo
+        // entries.  The fix-up of chunk ch (on st) waits for its tiles; the rows it completes
+        // also hold the partial sums of chunk ch - 1's tiles, which st waited for before.
+        cudaStream_t ts = c->cp_tile[ch % 2];
+        CK(cudaStreamWaitEvent(ts, ein, 0));
+        c->ops->jv_tiles(c, precision, dv, dy, L0 * ntxy, (L1 - L0) * ntxy, ts);
         CKLAUNCH();
+        CK(cudaEventRecord(c->tile_ev[ch % 8], ts));
+        CK(cudaStreamWaitEvent(st, c->tile_ev[ch % 8], 0));
         for (int cl = 0; cl < 3; ++cl) {
             const int64_t r0 = row_of(cl, fin_end * mxy), r1 = row_of(cl, fin * mxy);
             c->ops->fix_rows(c, precision, dy, r0, r1, st);

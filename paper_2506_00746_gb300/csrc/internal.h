@@ -220,7 +220,9 @@ struct fe_ctx {
     // fe_jacobian_action_host in z-chunks: copy streams, events, the fix-up rows' DOFs on the host
     bool chunked_host = true;
     cudaStream_t cp_in = nullptr, cp_out = nullptr;
+    cudaStream_t cp_tile[2] = { nullptr, nullptr };   // the chunks' tile kernels, alternately
     cudaEvent_t chunk_ev[17] = {};
+    cudaEvent_t tile_ev[8] = {};
     std::vector<uint32_t> h_fix_g;
     // captured CG batches: [0] FP64 operator and vectors, [1] FP32 operator with FP64 vectors,
     // [2] FP32 operator and vectors, [3] double-float operator with FP64 vectors
