@@ -1024,7 +1024,7 @@ struct Ops {
                 constexpr int TT = max_tile(3, D1 - 1);
                 const size_t tsm = res_tile_smem_bytes<D1, TT>();
                 const unsigned grid = (unsigned)c->ntiles;
-                constexpr int NTH = TileShape<D1, TT>::THREADS;
+                constexpr int NTH = TileShape<D1, TT>::CTHREADS;
                 const bool tan = T64 || T32;
                 double *halo = reinterpret_cast<double *>(c->d_halo);
                 {
@@ -1084,7 +1084,7 @@ struct Ops {
                                            reinterpret_cast<float *>(c->d_halo), (const TIO *)nullptr);
                     } else {
                         const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
-                        k_jv_tile<D1, TT, TC, TIO><<<grid, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                        k_jv_tile<D1, TT, TC, TIO><<<grid, TileShape<D1, TT>::CTHREADS, tsm, st>>>(
                             c->op, *bs, Tq, v, y, reinterpret_cast<TC *>(c->d_halo));
                     }
                 }
@@ -1132,9 +1132,11 @@ struct Ops {
             cudaFuncAttributes fa;
             e = cudaFuncGetAttributes(&fa, kern);
             if (e != cudaSuccess) return e;
-            if (fa.maxThreadsPerBlock < TileShape<D1, TT>::THREADS) return cudaSuccess;
+            // the packed FP32 kernel's block, or the collocated kernels' packed one
+            const int nth = sizeof(TC) == 4 ? TileShape<D1, TT>::THREADS : TileShape<D1, TT>::CTHREADS;
+            if (fa.maxThreadsPerBlock < nth) return cudaSuccess;
             int per_sm = 0;       // the launch must fit at least one CTA per SM
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TileShape<D1, TT>::THREADS, tsm);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nth, tsm);
             if (e != cudaSuccess) return e;
             if (per_sm < 1 || c->ntiles > 0x7fffffff) return cudaSuccess;
             c->pipe_grid[variant<TC, TIO>()] = (int)c->ntiles;     // one CTA per tile
@@ -1172,7 +1174,7 @@ struct Ops {
         c->res_tile = false;
         if constexpr (DIM == 3) {
             constexpr int TT = max_tile(3, D1 - 1);
-            constexpr int NTH = TileShape<D1, TT>::THREADS;
+            constexpr int NTH = TileShape<D1, TT>::CTHREADS;
             if (c->per_element || c->T != TT || c->ntiles > 0x7fffffff) return cudaSuccess;
             const size_t tsm = res_tile_smem_bytes<D1, TT>();
             if (tsm > (size_t)c->smem_optin) return cudaSuccess;
@@ -1207,12 +1209,12 @@ struct Ops {
             if constexpr (is_dfloat<TC>::value) {
                 LaunchScope ls(c, "jv_pa_df", st);
                 const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
-                k_jv_tile<D1, TT, TC, TIO><<<(unsigned)nt, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                k_jv_tile<D1, TT, TC, TIO><<<(unsigned)nt, TileShape<D1, TT>::CTHREADS, tsm, st>>>(
                     P, c->bdf, c->d_Tdf, v, y, reinterpret_cast<TC *>(c->d_halo));
             } else if constexpr (sizeof(TC) == 8) {
                 LaunchScope ls(c, "jv_pa_f64", st);
                 const size_t tsm = tile_smem_bytes<D1, TT, TC, TIO>(c->tqs64, c->Spad);
-                k_jv_tile<D1, TT, TC, TIO><<<(unsigned)nt, TileShape<D1, TT>::THREADS, tsm, st>>>(
+                k_jv_tile<D1, TT, TC, TIO><<<(unsigned)nt, TileShape<D1, TT>::CTHREADS, tsm, st>>>(
                     P, c->b64, c->d_T64, v, y, reinterpret_cast<TC *>(c->d_halo));
             } else {
                 LaunchScope ls(c, "jv_pa_f32", st);

@@ -11,8 +11,10 @@
 // neighbouring tile go to the halo buffer for the fix-up kernel.
 //
 // Threads: every line of a stage (e.g. the z-line of slots (sx, sy)) is split into its TT
-// element segments; segment h of all lines is handled by one group of warps (thread = line +
-// NLP * h), so the lanes of a warp walk consecutive lines.  A transposed stage leaves the seam
+// element segments; segment h of all lines is handled by one group of warps (packed FP32 kernel:
+// thread = line + NLP * h, NLP the line count of the x stage rounded up to 32; collocated
+// kernels: thread = line + lines * h with the stage's own line count, unpadded), so the lanes
+// of a warp walk consecutive lines.  A transposed stage leaves the seam
 // DOF between segments h and h+1 split: segment h+1's term in the array, segment h's term in a
 // small seam plane; the next stage adds them (left term first).  Shared-memory strides are
 // padded so that every access of a warp touches 32 distinct banks.
@@ -46,6 +48,11 @@ struct TileShape {
     static constexpr int NC = SE * QT * QT;        // one x-stage array (C, D)
     static constexpr int NLP = ((QT * QT + 31) / 32) * 32;   // lines per segment group
     static constexpr int THREADS = NLP * TT;
+    // the collocated (FP64, double-float, residual) kernels pack each stage's lines of all
+    // segments contiguously (thread = line + lines x h), so that a stage with fewer lines than a
+    // multiple of 32 per segment leaves idle lanes only at the end: every idle lane of an FP64
+    // warp instruction is FP64-unit time lost
+    static constexpr int CTHREADS = ((QT * QT * TT + 31) / 32) * 32;
     // seam planes (left terms of the DOFs shared by segments h and h+1)
     static constexpr int NSX = (TT - 1) * QT * QT; // per x-stage array
     static constexpr int NSY = (TT - 1) * QT * SE; // per y-stage array
@@ -136,8 +143,19 @@ template <int D1, int TT>
 struct Colloc {
     using TS = TileShape<D1, TT>;
     static constexpr int K = TS::K, Q1 = D1, SE = TS::SE, QT = TS::QT, NQT = TS::NQT;
-    static constexpr int SA = TS::SA, NLP = TS::NLP;
+    static constexpr int SA = TS::SA;
     __host__ __device__ static constexpr int pidx(int qx, int qy, int qz) { return qz + QT * (qy + QT * qx); }
+
+    // the packed thread mapping of a stage with NL lines per segment: thread tid takes line L of
+    // segment h, tid = L + NL h; false for threads past the stage's TT NL lines
+    template <int NL>
+    __host__ __device__ static bool line(int tid, int &L, int &h)
+    {
+        if (tid >= NL * TT) return false;
+        h = tid / NL;
+        L = tid - NL * h;
+        return true;
+    }
 
     // out[q] = sum_a B[q][a] in[a], each sum in ascending a; the Q1 sums advance together so that
     // their multiply-adds are independent of one another
@@ -155,8 +173,8 @@ struct Colloc {
     template <typename TC, typename TIO>
     __host__ __device__ static void z(const BasisT<TC> &Bs, const TIO *Vs, TC *A, int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= SE * SE) return;
+        int L, h;
+        if (!line<SE*SE>(tid, L, h)) return;
         const int sx = L % SE, sy = L / SE;
         TC in[D1];
 #pragma unroll
@@ -170,8 +188,8 @@ struct Colloc {
     template <typename TC>
     __host__ __device__ static void y(const BasisT<TC> &Bs, const TC *A, TC *C, int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= SE * QT) return;
+        int L, h;
+        if (!line<SE*QT>(tid, L, h)) return;
         const int sx = L % SE, qz = L / SE;
         TC in[D1];
 #pragma unroll
@@ -185,8 +203,8 @@ struct Colloc {
     template <typename TC>
     __host__ __device__ static void x1(const BasisT<TC> &Bs, const TC *C, TC *U, int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= QT * QT) return;
+        int L, h;
+        if (!line<QT*QT>(tid, L, h)) return;
         const int qz = L % QT, qy = L / QT;
         const int xo = SE * qz + SE * QT * qy + K * h;
         TC in[D1];
@@ -205,8 +223,8 @@ struct Colloc {
     __host__ __device__ static void x2(const BasisT<TC> &Bs, const TC *Tb, const TC *U, TC *fx, TC *FY, TC *FZ,
                                        int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= QT * QT) return;
+        int L, h;
+        if (!line<QT*QT>(tid, L, h)) return;
         const int qz = L % QT, qy = L / QT;
         const int y0 = Q1 * (qy / Q1), yl = qy % Q1, z0 = Q1 * (qz / Q1), zl = qz % Q1;
         const TC *Tl = Tb + Q1 * (qz + QT * (qy + QT * h));
@@ -251,8 +269,8 @@ struct Colloc {
     __host__ __device__ static void x3s(const BasisT<TC> &Bs, const TC *fx, const TC *s, const TC *FY,
                                         const TC *FZ, TC *C, TC *SX, int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= QT * QT) return;
+        int L, h;
+        if (!line<QT*QT>(tid, L, h)) return;
         const int qz = L % QT, qy = L / QT;
         const int y0 = Q1 * (qy / Q1), yl = qy % Q1, z0 = Q1 * (qz / Q1), zl = qz % Q1;
         const int xo = SE * qz + SE * QT * qy + K * h;
@@ -285,8 +303,8 @@ struct Colloc {
     template <typename TC>
     __host__ __device__ static void yT(const BasisT<TC> &Bs, const TC *C, const TC *SX, TC *A, TC *SY, int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= SE * QT) return;
+        int L, h;
+        if (!line<SE*QT>(tid, L, h)) return;
         const int sx = L % SE, qz = L / SE;
         const bool xseam = (sx % K == 0) && sx > 0 && sx < SE - 1;
         TC e[Q1];
@@ -314,8 +332,8 @@ struct Colloc {
     __host__ __device__ static void zT(const BasisT<TC> &Bs, const TC *A, const TC *SY, TC *SZ, const W &write,
                                        TC &out0, int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= SE * SE) return;
+        int L, h;
+        if (!line<SE*SE>(tid, L, h)) return;
         const int zx = L % SE, zy = L / SE;
         const bool yseam = (zy % K == 0) && zy > 0 && zy < SE - 1;
         TC zv[Q1];
@@ -344,8 +362,8 @@ struct Colloc {
     template <typename TC, typename W>
     __host__ __device__ static void seam(const TC *SZ, const W &write, TC out0, int tid)
     {
-        const int L = tid % NLP, h = tid / NLP;
-        if (L >= SE * SE || h == 0) return;
+        int L, h;
+        if (!line<SE * SE>(tid, L, h) || h == 0) return;
         write((K * h * SE + L / SE) * SE + L % SE, SZ[(h - 1) * SE * SE + L] + out0);
     }
 };
@@ -382,14 +400,14 @@ template <int THREADS>
 constexpr int tile_min_blocks() { return THREADS <= 128 ? 512 / THREADS : 1; }
 
 template <int D1, int TT, typename TC, typename TIO>
-__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<TileShape<D1, TT>::THREADS>())
+__global__ void __launch_bounds__(TileShape<D1, TT>::CTHREADS, tile_min_blocks<TileShape<D1, TT>::CTHREADS>())
     k_jv_tile(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<TC> Bs, const TC *__restrict__ Tq,
               const TIO *__restrict__ v, TIO *__restrict__ y, TC *__restrict__ halo)
 {
     using TS = TileShape<D1, TT>;
     using S = Colloc<D1, TT>;
     constexpr int NS3 = TS::NS3, NSX = TS::NSX, NSY = TS::NSY;
-    constexpr int NTH = TS::THREADS;
+    constexpr int NTH = TS::CTHREADS;
     if (P.skip && *P.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t t = P.t0 + blockIdx.x;

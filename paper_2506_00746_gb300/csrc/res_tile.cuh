@@ -56,10 +56,10 @@ __device__ __forceinline__ void res_x2(const OpParams &P, const BasisT<double> &
                                        double *__restrict__ T64, float *__restrict__ T32, int tid)
 {
     using S = Colloc<D1, TT>;
-    constexpr int Q1 = D1, QT = S::QT, NQT = S::NQT, NLP = S::NLP;
+    constexpr int Q1 = D1, QT = S::QT, NQT = S::NQT;
     constexpr int NQ = D1 * D1 * D1, NE = TT * TT * TT;
-    const int L = tid % NLP, h = tid / NLP;
-    if (L >= QT * QT) return;
+    int L, h;
+    if (!S::template line<QT * QT>(tid, L, h)) return;
     const int qz = L % QT, qy = L / QT;
     const int ey = qy / Q1, yl = qy % Q1, ez = qz / Q1, zl = qz % Q1;
     const int y0 = Q1 * ey, z0 = Q1 * ez;
@@ -127,14 +127,14 @@ __device__ __forceinline__ void res_x2(const OpParams &P, const BasisT<double> &
 
 // One CTA per tile.  RES: write R(u) (halo partial sums for the fix-up); TAN: store the tangent.
 template <int D1, int TT, bool RES, bool TAN>
-__global__ void __launch_bounds__(TileShape<D1, TT>::THREADS, tile_min_blocks<TileShape<D1, TT>::THREADS>())
+__global__ void __launch_bounds__(TileShape<D1, TT>::CTHREADS, tile_min_blocks<TileShape<D1, TT>::CTHREADS>())
     k_res_tile(const __grid_constant__ OpParams P, const __grid_constant__ BasisT<double> Bs,
                const double *__restrict__ u, double *__restrict__ r, double *__restrict__ halo,
                double *__restrict__ T64, float *__restrict__ T32)
 {
     using TS = TileShape<D1, TT>;
     using S = Colloc<D1, TT>;
-    constexpr int NS3 = TS::NS3, NSX = TS::NSX, NSY = TS::NSY, NTH = TS::THREADS;
+    constexpr int NS3 = TS::NS3, NSX = TS::NSX, NSY = TS::NSY, NTH = TS::CTHREADS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t t = P.t0 + blockIdx.x;
     const int tid = threadIdx.x;

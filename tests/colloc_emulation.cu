@@ -65,16 +65,16 @@ double run(unsigned seed, bool reverse)
     double *SX = Tbs, *SY = SX + TS::NSX, *SZ = SY + TS::NSY;
     for (int s = 0; s < NS3; ++s) Vss[s] = Vs[s];
     for (int i = 0; i < 6 * NQT; ++i) Tbs[i] = Tb[i];
-    std::vector<double> fxs((size_t)TS::THREADS * Q1, nan);     // each thread's registers
+    std::vector<double> fxs((size_t)TS::CTHREADS * Q1, nan);     // each thread's registers
     std::vector<uint32_t> codes(NS3), hd(NS3, 0);
     for (int s = 0; s < NS3; ++s) codes[s] = (uint32_t)s;
-    std::vector<double> v(NS3, 0.0), y(NS3, nan), halo(1, 0.0), out0(TS::THREADS, 0.0);
+    std::vector<double> v(NS3, 0.0), y(NS3, nan), halo(1, 0.0), out0(TS::CTHREADS, 0.0);
     std::vector<int> writes(NS3, 0);
     struct CountingWriter {
         SlotWriter<double, double> w; int *cnt;
         void operator()(int s, double val) const { cnt[s]++; w(s, val); }
     } write{ SlotWriter<double, double>{ codes.data(), hd.data(), v.data(), y.data(), halo.data() }, writes.data() };
-    const int NT = TS::THREADS;
+    const int NT = TS::CTHREADS;
     // threads of a stage in ascending or descending order: a write of one thread that another
     // thread of the same stage still reads shows in one of the two orders
     auto each = [&](auto &&stage) {
