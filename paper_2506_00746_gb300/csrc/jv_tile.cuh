@@ -49,9 +49,9 @@ struct TileShape {
     static constexpr int NLP = ((QT * QT + 31) / 32) * 32;   // lines per segment group
     static constexpr int THREADS = NLP * TT;
     // the collocated (FP64, double-float, residual) kernels pack each stage's lines of all
-    // segments contiguously (thread = line + lines x h), so that a stage with fewer lines than a
-    // multiple of 32 per segment leaves idle lanes only at the end: every idle lane of an FP64
-    // warp instruction is FP64-unit time lost
+    // segments contiguously (thread = line + lines x h) where that takes fewer warps, so that a
+    // stage with fewer lines than a multiple of 32 per segment leaves idle lanes only at the end:
+    // every idle lane of an FP64 warp instruction is FP64-unit time lost (Colloc::line)
     static constexpr int CTHREADS = ((QT * QT * TT + 31) / 32) * 32;
     // seam planes (left terms of the DOFs shared by segments h and h+1)
     static constexpr int NSX = (TT - 1) * QT * QT; // per x-stage array
@@ -146,15 +146,18 @@ struct Colloc {
     static constexpr int SA = TS::SA;
     __host__ __device__ static constexpr int pidx(int qx, int qy, int qz) { return qz + QT * (qy + QT * qx); }
 
-    // the packed thread mapping of a stage with NL lines per segment: thread tid takes line L of
-    // segment h, tid = L + NL h; false for threads past the stage's TT NL lines
+    // the thread mapping of a stage with NL lines per segment: thread tid takes line L of segment
+    // h, tid = L + ST h, false for a thread without a line.  ST = NL (packed) where that takes
+    // fewer warps than one warp-aligned group per segment; otherwise ST = NL rounded up to 32
+    // (the same warps, and no lane of a warp shared by two segments)
     template <int NL>
     __host__ __device__ static bool line(int tid, int &L, int &h)
     {
-        if (tid >= NL * TT) return false;
-        h = tid / NL;
-        L = tid - NL * h;
-        return true;
+        constexpr int R = (NL + 31) / 32 * 32;
+        constexpr int ST = (TT * NL + 31) / 32 * 32 < TT * R ? NL : R;
+        h = tid / ST;
+        L = tid - ST * h;
+        return h < TT && L < NL;
     }
 
     // out[q] = sum_a B[q][a] in[a], each sum in ascending a; the Q1 sums advance together so that
