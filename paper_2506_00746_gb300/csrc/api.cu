@@ -631,6 +631,20 @@ static fe_status setup_impl(fe_ctx *c, const fe_mesh *mesh, int order, const fe_
         c->b32.Dc[i] = (float)cder[i];
         c->bdf.Dc[i] = dfloat(cder[i]);
     }
+    // packed double-float coefficient pairs (rows i, i + 1; an odd last row paired with 0)
+    {
+        const int d1 = c->d1, q1 = c->q1;
+        const dfloat z(0);
+        auto fill = [&](df2c *t, int ni, int nk, auto m) {
+            for (int i = 0; i < ni; i += 2)
+                for (int k = 0; k < nk; ++k)
+                    t[(i / 2) * MAXQ + k] = df2c_pack(m(i, k), i + 1 < ni ? m(i + 1, k) : z);
+        };
+        fill(c->bdf.pk.Bq, q1, d1, [&](int i, int k) { return c->bdf.B[i * d1 + k]; });
+        fill(c->bdf.pk.Bt, d1, q1, [&](int i, int k) { return c->bdf.B[k * d1 + i]; });
+        fill(c->bdf.pk.Dq, q1, q1, [&](int i, int k) { return c->bdf.Dc[i * q1 + k]; });
+        fill(c->bdf.pk.Dt, q1, q1, [&](int i, int k) { return c->bdf.Dc[k * q1 + i]; });
+    }
     c->gp.dim = dim; c->gp.d1 = c->d1; c->gp.q1 = c->q1; c->gp.T = T;
     for (int d = 0; d < 3; ++d) { c->gp.n[d] = n[d]; c->gp.nt[d] = c->nt[d]; }
     c->gp.nepad = c->nepad; c->gp.f_kind = prob->f_kind; c->gp.f_const = prob->f_const; c->gp.p = prob->p;

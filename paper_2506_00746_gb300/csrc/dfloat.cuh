@@ -76,6 +76,89 @@ __device__ __forceinline__ dfloat operator+(dprod x, dprod y) { return df_add(x.
 __device__ __forceinline__ dfloat &operator+=(dfloat &x, dfloat y) { return x = x + y; }
 __device__ __forceinline__ dfloat &operator+=(dfloat &x, dprod y) { return x = x + y; }
 
+// Two independent dfloats in the two lanes of float2 words, for the packed FP32 instructions
+// (fma.rn.f32x2, add.rn.f32x2, mul.rn.f32x2): one packed instruction does the work of two scalar
+// ones, and each lane's result is bit for bit that of the scalar operation on that lane.
+struct df2 {
+    float2 h, l;
+};
+
+// A packed coefficient: high words, low words and negated high words (a product's high term is
+// formed negated where its exact error needs -p, since there is no packed subtraction).
+struct df2c {
+    float2 h, l, nh;
+};
+
+__host__ __device__ inline df2c df2c_pack(dfloat a, dfloat b)
+{
+    return df2c{ make_float2(a.h, b.h), make_float2(a.l, b.l), make_float2(-a.h, -b.h) };
+}
+
+// the packed two-lane FP32 instructions exist on sm_100 and later (device code only)
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define FEOD_F32X2 1
+#endif
+
+#ifdef FEOD_F32X2
+__device__ __forceinline__ df2 df2_bcast(dfloat x) { return df2{ make_float2(x.h, x.h), make_float2(x.l, x.l) }; }
+__device__ __forceinline__ df2c df2c_bcast(dfloat x)
+{
+    return df2c{ make_float2(x.h, x.h), make_float2(x.l, x.l), make_float2(-x.h, -x.h) };
+}
+__device__ __forceinline__ df2 df2_pack(dfloat a, dfloat b) { return df2{ make_float2(a.h, b.h), make_float2(a.l, b.l) }; }
+__device__ __forceinline__ dfloat df2_lo(const df2 &v) { dfloat r; r.h = v.h.x; r.l = v.l.x; return r; }
+__device__ __forceinline__ dfloat df2_hi(const df2 &v) { dfloat r; r.h = v.h.y; r.l = v.l.y; return r; }
+__device__ __forceinline__ df2 df2_zero() { return df2{ make_float2(0.f, 0.f), make_float2(0.f, 0.f) }; }
+
+// fl(a - b) lane by lane: fma(b, -1, a) rounds a - b once, as a scalar subtraction does
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// acc += c x lane by lane (the scalar acc + c * x: the product of Joldes, Muller and Popescu
+// without normalisation, then the compensated sum)
+__device__ __forceinline__ void df2_fma(df2 &acc, const df2c &c, const df2 &x)
+{
+    const float2 np = __fmul2_rn(c.nh, x.h);          // -fl(ch xh)
+    float2 e = __ffma2_rn(c.h, x.h, np);              // ch xh - p, exact
+    e = __ffma2_rn(c.h, x.l, e);
+    e = __ffma2_rn(c.l, x.h, e);
+    // two_sum(acc.h, p) with p = -np: s = fl(acc.h + p), bb = s - acc.h,
+    // err = (acc.h - (s - bb)) + (p - bb)
+    const float2 s = sub2(acc.h, np);
+    const float2 bb = sub2(s, acc.h);
+    const float2 e1 = sub2(acc.h, sub2(s, bb));
+    const float2 e2 = __fadd2_rn(np, bb);             // -(p - bb)
+    const float2 es = sub2(e1, e2);
+    acc.l = __fadd2_rn(es, __fadd2_rn(acc.l, e));
+    acc.h = s;
+}
+
+// the unnormalised product t g lane by lane (the scalar t * g), given ngh = -g.h
+struct dprod2 {
+    float2 p, e;
+};
+__device__ __forceinline__ dprod2 df2_mul(const df2 &t, const df2 &g, float2 ngh)
+{
+    dprod2 r;
+    r.p = __fmul2_rn(t.h, g.h);
+    const float2 np = __fmul2_rn(t.h, ngh);            // -p exactly
+    float2 e = __ffma2_rn(t.h, g.h, np);
+    e = __ffma2_rn(t.h, g.l, e);
+    r.e = __ffma2_rn(t.l, g.h, e);
+    return r;
+}
+
+// (a1 + a2) + (b1 + b2) lane by lane, as df_add
+__device__ __forceinline__ df2 df2_add(float2 a1, float2 a2, float2 b1, float2 b2)
+{
+    df2 r;
+    r.h = __fadd2_rn(a1, b1);
+    const float2 bb = sub2(r.h, a1);
+    const float2 e = __fadd2_rn(sub2(a1, sub2(r.h, bb)), sub2(b1, bb));
+    r.l = __fadd2_rn(e, __fadd2_rn(a2, b2));
+    return r;
+}
+#endif
+
 template <typename T>
 struct is_dfloat { static constexpr bool value = false; };
 template <>

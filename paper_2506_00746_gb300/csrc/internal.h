@@ -39,6 +39,20 @@ constexpr uint32_t SLOT_HALO = 0x80000000u;
 constexpr uint32_t SLOT_INVALID = 0xFFFFFFFFu;
 constexpr int64_t MAX_DOFS = (int64_t)SLOT_GMASK;   // 2^30 - 1
 
+// Packed coefficient pairs of the double-float stages (empty for other types).  Each table pairs
+// the rows i, i + 1 of a matrix M at column k, entry [(i / 2) MAXQ + k] (an odd last row with 0):
+//   Bq:  M = B        (interpolation, i < Q1, k < D1)
+//   Bt:  M = B^T      (transposed interpolation, i < D1, k < Q1)
+//   Dq:  M = Dc       (collocation derivative, i, k < Q1)
+//   Dt:  M = Dc^T
+constexpr int NPK = (MAXQ + 1) / 2 * MAXQ;
+template <typename T>
+struct DfPairsT {};
+template <>
+struct DfPairsT<dfloat> {
+    df2c Bq[NPK], Bt[NPK], Dq[NPK], Dt[NPK];
+};
+
 // 1D basis tables on the reference interval [0,1], row-major [q][a] with q < Q1, a < D1:
 // B = phi_a(xi_q), G = phi_a'(xi_q), and the products used by the Jacobi diagonal.
 template <typename T>
@@ -49,6 +63,7 @@ struct BasisT {
     T G2[MAXQ * MAXQ];   // G^2
     T BG[MAXQ * MAXQ];   // B*G
     T Dc[MAXQ * MAXQ];   // collocation derivative at the Gauss points: Dc[q][j] = l_j'(x_q)
+    DfPairsT<T> pk;
 };
 
 // FP32 1D basis tables as pairs, for packed (two-lane) FP32 multiply-adds: BG = (B, G),
