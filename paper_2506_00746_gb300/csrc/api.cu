@@ -758,6 +758,7 @@ extern "C" void fe_destroy(fe_ctx *c)
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->cp_in) cudaStreamDestroy(c->cp_in);
     if (c->cp_out) cudaStreamDestroy(c->cp_out);
+    if (c->cp_fix) cudaStreamDestroy(c->cp_fix);
     for (cudaStream_t t : c->cp_tile)
         if (t) cudaStreamDestroy(t);
     for (cudaEvent_t e : c->chunk_ev)
@@ -886,7 +887,12 @@ fe_status jv_host_chunked(fe_ctx *c, const void *v_host, void *y_host, int preci
     if (!c->cp_in) {
         CK(cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking));
-        for (auto &t : c->cp_tile) CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+        // a chunk's fix-up takes the SM slots that free up before the next chunk's pending tiles
+        // do, so that its rows go back to the host while that chunk computes
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        for (auto &t : c->cp_tile) CK(cudaStreamCreateWithPriority(&t, cudaStreamNonBlocking, lo));
+        CK(cudaStreamCreateWithPriority(&c->cp_fix, cudaStreamNonBlocking, hi));
         for (auto &e : c->chunk_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         for (auto &e : c->tile_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
@@ -915,20 +921,20 @@ fe_status jv_host_chunked(fe_ctx *c, const void *v_host, void *y_host, int preci
         CK(cudaEventRecord(ein, c->cp_in));
         // the chunks' tile kernels alternate between two streams, so that one chunk's last wave
         // of tiles runs beside the next chunk's first: they write disjoint owned rows and halo
-        // entries.  The fix-up of chunk ch (on st) waits for its tiles; the rows it completes
-        // also hold the partial sums of chunk ch - 1's tiles, which st waited for before.
+        // entries.  The fix-up of chunk ch (on cp_fix) waits for its tiles; the rows it completes
+        // also hold the partial sums of chunk ch - 1's tiles, which cp_fix waited for before.
         cudaStream_t ts = c->cp_tile[ch % 2];
         CK(cudaStreamWaitEvent(ts, ein, 0));
         c->ops->jv_tiles(c, precision, dv, dy, L0 * ntxy, (L1 - L0) * ntxy, ts);
         CKLAUNCH();
         CK(cudaEventRecord(c->tile_ev[ch % 8], ts));
-        CK(cudaStreamWaitEvent(st, c->tile_ev[ch % 8], 0));
+        CK(cudaStreamWaitEvent(c->cp_fix, c->tile_ev[ch % 8], 0));
         for (int cl = 0; cl < 3; ++cl) {
             const int64_t r0 = row_of(cl, fin_end * mxy), r1 = row_of(cl, fin * mxy);
-            c->ops->fix_rows(c, precision, dy, r0, r1, st);
+            c->ops->fix_rows(c, precision, dy, r0, r1, c->cp_fix);
         }
         CKLAUNCH();
-        CK(cudaEventRecord(efin, st));
+        CK(cudaEventRecord(efin, c->cp_fix));
         CK(cudaStreamWaitEvent(c->cp_out, efin, 0));
         if (fin > fin_end) {
             CK(cudaMemcpyAsync((char *)y_host + fin_end * mxy * es, (const char *)dy + fin_end * mxy * es,

@@ -236,6 +236,7 @@ struct fe_ctx {
     bool chunked_host = true;
     cudaStream_t cp_in = nullptr, cp_out = nullptr;
     cudaStream_t cp_tile[2] = { nullptr, nullptr };   // the chunks' tile kernels, alternately
+    cudaStream_t cp_fix = nullptr;                    // the chunks' fix-ups (high priority)
     cudaEvent_t chunk_ev[17] = {};
     cudaEvent_t tile_ev[8] = {};
     std::vector<uint32_t> h_fix_g;
