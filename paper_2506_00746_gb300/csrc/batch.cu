@@ -557,6 +557,11 @@ struct fe_batch {
     float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fq = nullptr, *dinv = nullptr;
     double *R = nullptr, *Rt = nullptr, *B = nullptr, *D = nullptr, *diag = nullptr;
     cudaStream_t st = nullptr;
+    // policy 3: each variant's launch on a stream of its own between a fork and a join on the
+    // caller's stream, so that the launches run side by side (they write disjoint rows and halo
+    // entries) instead of each waiting for the previous one's last wave
+    cudaStream_t vst[NBV] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[NBV] = {};
     cudaGraphExec_t cg_exec = nullptr;    // one CG batch (use_graph 1)
     int cg_batch = 0;
     cudaGraphExec_t cg_loop = nullptr;    // the whole CG on the device (use_graph 2)
@@ -752,12 +757,17 @@ fe_status launch_jv(fe_batch *b, const float *vb, float *yb, bool with_skip, cud
     for (int v = 0; v <= NBV; ++v) W.vbeg[v] = b->vbeg[v];
     W.start = b->d_start;
     if (b->policy == 3) {
+        BCK(cudaEventRecord(b->fork_ev, st));
         for (int v = 0; v < NBV; ++v) {
             const int nv = b->vbeg[v + 1] - b->vbeg[v];
             if (nv == 0) continue;
             const int2 *items = b->d_items + b->vbeg[v];
             void *args[] = { (void *)&inst, (void *)&items, (void *)&vb, (void *)&yb, (void *)&b->d_err };
-            BCK(cudaLaunchKernel(bv_kernel(v), dim3((unsigned)nv), dim3((unsigned)bv_threads(v)), args, b->vsmem[v], st));
+            BCK(cudaStreamWaitEvent(b->vst[v], b->fork_ev, 0));
+            BCK(cudaLaunchKernel(bv_kernel(v), dim3((unsigned)nv), dim3((unsigned)bv_threads(v)), args, b->vsmem[v],
+                                 b->vst[v]));
+            BCK(cudaEventRecord(b->join_ev[v], b->vst[v]));
+            BCK(cudaStreamWaitEvent(st, b->join_ev[v], 0));
             b->launches += 1;
         }
     } else {
@@ -993,6 +1003,11 @@ extern "C" fe_status fe_batch_create(const fe_batch_item *items, int count, cons
     b->variant.resize(count);
     for (int i = 0; i < count; ++i) b->order[i] = items[i].order;
     fe_status s = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+    for (int v = 0; v < NBV && s == FE_OK; ++v)
+        if (cudaStreamCreateWithFlags(&b->vst[v], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join_ev[v], cudaEventDisableTiming) != cudaSuccess)
+            s = FE_ERR_CUDA;
+    if (s == FE_OK && cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) s = FE_ERR_CUDA;
 
     // --- tile edge per order: fixed by opts, from the cache, or measured ---
     TuneCache cache;
@@ -1118,6 +1133,11 @@ extern "C" void fe_batch_destroy(fe_batch *b)
     free_batch_device(b);
     if (b->h_state) cudaFreeHost(b->h_state);
     if (b->st) cudaStreamDestroy(b->st);
+    for (int v = 0; v < NBV; ++v) {
+        if (b->vst[v]) cudaStreamDestroy(b->vst[v]);
+        if (b->join_ev[v]) cudaEventDestroy(b->join_ev[v]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     for (fe_ctx *c : b->ctx) fe_destroy(c);
     delete b;
 }
