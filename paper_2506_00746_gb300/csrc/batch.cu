@@ -258,8 +258,11 @@ struct BatchFix {
     int64_t off;
 };
 
+// blk_inst: per block, the instance of its first row (the largest i with row0[i] <= that row); a
+// row's instance is found from there by a forward scan over row0 (a block's rows span few
+// instances) instead of a binary search over all of them
 __global__ void k_fixup_batch(const BatchFix *__restrict__ bf, const int64_t *__restrict__ row0, int count,
-                              float *__restrict__ yb, unsigned *counter)
+                              const int *__restrict__ blk_inst, float *__restrict__ yb, unsigned *counter)
 {
     // the batched action before this kernel has taken all its items: reset its counters
     if (blockIdx.x == 0 && threadIdx.x < NBV) counter[threadIdx.x] = 0u;
@@ -274,11 +277,8 @@ __global__ void k_fixup_batch(const BatchFix *__restrict__ bf, const int64_t *__
         const int64_t r = rb + (int64_t)i * blockDim.x;
         j0[i] = j1[i] = 0u; g[i] = 0u; yp[i] = yb; hp[i] = nullptr;
         if (r >= nrows) continue;
-        int lo = 0, hi = count;          // row0[lo] <= r < row0[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) / 2;
-            if (row0[mid] <= r) lo = mid; else hi = mid;
-        }
+        int lo = blk_inst[blockIdx.x];   // the largest lo with row0[lo] <= r
+        while (lo + 1 < count && row0[lo + 1] <= r) ++lo;
         const BatchFix &B = bf[lo];
         if (B.fix.skip && *B.fix.skip) continue;
         const int64_t rr = r - row0[lo];
@@ -546,6 +546,7 @@ struct fe_batch {
     unsigned *d_counter = nullptr;        // per-variant item counters of the batched action
     BatchFix *d_fix = nullptr;            // same two copies
     int64_t *d_row0 = nullptr;
+    int *d_fix_blk = nullptr;             // per fix-up block, the instance of its first row
     int64_t nrows = 0;
     int *d_seg_inst = nullptr, *d_blk0 = nullptr;
     int64_t *d_seg_lo = nullptr, *d_seg_hi = nullptr, *d_len = nullptr;
@@ -662,12 +663,13 @@ struct TuneCache {
 
 void free_batch_device(fe_batch *b)
 {
-    void *ptrs[] = { b->d_inst, b->d_items, b->d_start, b->d_counter, b->d_fix, b->d_row0, b->d_seg_inst, b->d_blk0, b->d_seg_lo, b->d_seg_hi,
+    void *ptrs[] = { b->d_inst, b->d_items, b->d_start, b->d_counter, b->d_fix, b->d_row0, b->d_fix_blk, b->d_seg_inst, b->d_blk0, b->d_seg_lo, b->d_seg_hi,
                      b->d_len, b->d_active, b->d_err, b->d_state, b->d_partial, b->fx, b->fr, b->fp, b->fq, b->dinv,
                      b->R, b->Rt, b->B, b->D, b->diag };
     for (void *p : ptrs)
         if (p) cudaFree(p);
     b->d_inst = nullptr; b->d_items = nullptr; b->d_start = nullptr; b->d_counter = nullptr; b->d_fix = nullptr; b->d_row0 = nullptr; b->d_seg_inst = nullptr;
+    b->d_fix_blk = nullptr;
     b->d_blk0 = nullptr; b->d_seg_lo = nullptr; b->d_seg_hi = nullptr; b->d_len = nullptr; b->d_active = nullptr;
     b->d_err = nullptr; b->d_state = nullptr; b->d_partial = nullptr; b->fx = b->fr = b->fp = b->fq = b->dinv = nullptr;
     b->R = b->Rt = b->B = b->D = b->diag = nullptr;
@@ -775,7 +777,7 @@ fe_status launch_jv(fe_batch *b, const float *vb, float *yb, bool with_skip, cud
         b->launches += 1;
     }
     const unsigned fb = (unsigned)std::max<int64_t>(1, (b->nrows + 256 * FIX_ROWS - 1) / (256 * FIX_ROWS));
-    k_fixup_batch<<<fb, 256, 0, st>>>(fix, b->d_row0, b->count, yb, b->d_counter);
+    k_fixup_batch<<<fb, 256, 0, st>>>(fix, b->d_row0, b->count, b->d_fix_blk, yb, b->d_counter);
     b->launches += 1;
     BCK(cudaGetLastError());
     return FE_OK;
@@ -863,6 +865,18 @@ fe_status build_tables(fe_batch *b)
     BCK(cudaMemcpy(b->d_fix, hf.data(), hf.size() * sizeof(BatchFix), cudaMemcpyHostToDevice));
     BCK(balloc(&b->d_row0, n + 1));
     BCK(cudaMemcpy(b->d_row0, row0.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    {
+        // the fix-up's blocks take 256 FIX_ROWS consecutive rows each (launch_jv)
+        const int64_t per = 256 * FIX_ROWS, nb = std::max<int64_t>(1, (b->nrows + per - 1) / per);
+        std::vector<int> fb((size_t)nb);
+        int lo = 0;
+        for (int64_t j = 0; j < nb; ++j) {
+            while (lo + 1 < n && row0[lo + 1] <= j * per) ++lo;
+            fb[(size_t)j] = lo;
+        }
+        BCK(balloc(&b->d_fix_blk, nb));
+        BCK(cudaMemcpy(b->d_fix_blk, fb.data(), (size_t)nb * sizeof(int), cudaMemcpyHostToDevice));
+    }
     // segments of the vector kernels
     std::vector<int> sinst, blk0(n + 1, 0);
     std::vector<int64_t> slo, shi;
