@@ -239,9 +239,35 @@ struct Colloc {
             for (int a = 0; a < D1; ++a) out[a] += Bs.B[q * D1 + a] * in[q];
     }
 
+    // FP64 z and y stages: one output point of a line per work unit (each sum still over a
+    // ascending), the units of all segments on consecutive threads in rounds of CTHREADS.  With one
+    // line per thread the last warp of a segment's lines runs its Q1 D1 multiply-adds for a few
+    // lanes (order 3: 49 z-lines of a segment in two warps); FP64 instructions cost their full
+    // issue whatever the lanes, so the units waste fewer (order 3: 52 + 56 instead of 64 + 64 FP64
+    // warp-instructions per tile for the 49 + 56 of useful work).
+    template <typename TC>
+    static constexpr bool UNITS = std::is_same<TC, double>::value;
+
     template <typename TC, typename TIO>
     __host__ __device__ static void z(const BasisT<TC> &Bs, const TIO *Vs, TC *A, int tid)
     {
+        if constexpr (UNITS<TC>) {
+            // unit u = sx + SE (qq + QT sy), qq = Q1 h + q: consecutive threads, consecutive slots
+            constexpr int NU = SE * QT * SE, NR = (NU + TS::CTHREADS - 1) / TS::CTHREADS;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int u = tid + i * TS::CTHREADS;
+                if (u < NU) {
+                    const int sx = u % SE, w = u / SE, qq = w % QT, sy = w / QT;
+                    const int h = qq / Q1, q = qq - Q1 * h;
+                    TC acc = TC(0);
+#pragma unroll
+                    for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * (TC)Vs[((K * h + a) * SE + sy) * SE + sx];
+                    A[sx + SE * qq + SA * sy] = acc;
+                }
+            }
+            return;
+        }
         int L, h;
         if (!line<SE*SE>(tid, L, h)) return;
         const int sx = L % SE, sy = L / SE;
@@ -257,6 +283,23 @@ struct Colloc {
     template <typename TC>
     __host__ __device__ static void y(const BasisT<TC> &Bs, const TC *A, TC *C, int tid)
     {
+        if constexpr (UNITS<TC>) {
+            // unit u = (sx + SE qz) + SE QT qq, qq = Q1 h + q: the output's own index in C
+            constexpr int NU = SE * QT * QT, NR = (NU + TS::CTHREADS - 1) / TS::CTHREADS;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int u = tid + i * TS::CTHREADS;
+                if (u < NU) {
+                    const int xz = u % (SE * QT), qq = u / (SE * QT);
+                    const int h = qq / Q1, q = qq - Q1 * h;
+                    TC acc = TC(0);
+#pragma unroll
+                    for (int a = 0; a < D1; ++a) acc += Bs.B[q * D1 + a] * A[xz + SA * (K * h + a)];
+                    C[u] = acc;
+                }
+            }
+            return;
+        }
         int L, h;
         if (!line<SE*QT>(tid, L, h)) return;
         const int sx = L % SE, qz = L / SE;
