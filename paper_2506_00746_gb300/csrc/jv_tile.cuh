@@ -65,8 +65,8 @@ struct TileShape {
 //       by y);
 //   U, the values at the points (written by x1, read by x2) lies inside A (read by y, next
 //       written by yT);
-//   the seam planes SX, SY, SZ (written from x3 on) lie inside the tangent block Tb (last read
-//       by x2).
+//   the seam planes SX, SY, SZ and S0 (written from x3 on) lie inside the tangent block Tb (last
+//       read by x2).
 // FX, the x-component of the flux, stays in registers: x2 and x3 map a thread to the same points.
 template <int D1, int TT, typename TC, typename TIO>
 struct TileLayout {
@@ -74,7 +74,7 @@ struct TileLayout {
     static constexpr size_t A_BYTES = pad16((size_t)(TS::NA > TS::NQT ? TS::NA : TS::NQT) * sizeof(TC));
     static constexpr size_t C_BYTES = pad16((size_t)TS::NC * sizeof(TC) > (size_t)TS::NS3 * sizeof(TIO)
                                                 ? (size_t)TS::NC * sizeof(TC) : (size_t)TS::NS3 * sizeof(TIO));
-    static constexpr size_t SEAM_ELEMS = (size_t)TS::NSX + TS::NSY + TS::NSZ;
+    static constexpr size_t SEAM_ELEMS = (size_t)TS::NSX + TS::NSY + 2 * TS::NSZ;   // SX, SY, SZ, S0
     size_t tb, codes, hd, a, c, fy, fz, total;
     __host__ __device__ explicit TileLayout(int64_t tqs)
     {
@@ -487,9 +487,63 @@ struct Colloc {
         else SX[h * QT * QT + L] = d[K];
     }
 
+    // FP64 backward half: the seam terms are added once, in place, before the stage that reads
+    // them (the units of yT and zT then run without a branch that every warp would issue): C at
+    // the x-seam slots sx = K m gets SX (left term first, as yT adds it), after x3; A at the y-seam
+    // slots gets SY, after yT.
     template <typename TC>
+    __host__ __device__ static void foldx(TC *C, const TC *SX, int tid)
+    {
+        constexpr int NU = TS::NSX, NR = (NU + TS::CTHREADS - 1) / TS::CTHREADS;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int u = tid + i * TS::CTHREADS;       // u = qz + QT qy + QT QT (m - 1)
+            if (u < NU) {
+                const int qzy = u % (QT * QT), m = u / (QT * QT) + 1, qz = qzy % QT, qy = qzy / QT;
+                TC &c = C[K * m + SE * qz + SE * QT * qy];
+                c = SX[u] + c;
+            }
+        }
+    }
+    template <typename TC>
+    __host__ __device__ static void foldy(TC *A, const TC *SY, int tid)
+    {
+        constexpr int NU = TS::NSY, NR = (NU + TS::CTHREADS - 1) / TS::CTHREADS;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int u = tid + i * TS::CTHREADS;       // u = zx + SE qz + SE QT (m - 1)
+            if (u < NU) {
+                const int xz = u % (SE * QT), m = u / (SE * QT) + 1;
+                TC &a = A[xz + SA * (K * m)];
+                a = SY[u] + a;
+            }
+        }
+    }
+
+    // U: the unit mapping (the caller has run foldx), else one line per thread with the seam
+    // terms added here
+    template <typename TC, bool U = UNITS<TC>>
     __host__ __device__ static void yT(const BasisT<TC> &Bs, const TC *C, const TC *SX, TC *A, TC *SY, int tid)
     {
+        if constexpr (U) {
+            // one output node a of a line per unit (C's x-seams folded in by foldx), unit
+            // u = xz + SE QT (a + D1 h), xz = sx + SE qz
+            constexpr int NU = SE * QT * D1 * TT, NR = (NU + TS::CTHREADS - 1) / TS::CTHREADS;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int u = tid + i * TS::CTHREADS;
+                if (u < NU) {
+                    const int xz = u % (SE * QT), w = u / (SE * QT), a = w % D1, h = w / D1;
+                    TC acc = TC(0);
+#pragma unroll
+                    for (int q = 0; q < Q1; ++q) acc += Bs.B[q * D1 + a] * C[xz + SE * QT * (Q1 * h + q)];
+                    if (a < K) A[xz + SA * (K * h + a)] = acc;
+                    else if (h == TT - 1) A[xz + SA * (SE - 1)] = acc;
+                    else SY[h * QT * SE + xz] = acc;
+                }
+            }
+            return;
+        }
         int L, h;
         if (!line<SE*QT>(tid, L, h)) return;
         const int sx = L % SE, qz = L / SE;
@@ -510,10 +564,35 @@ struct Colloc {
     }
 
     // out0: this thread's term of slot K h, added by seam() after the next barrier (h > 0)
-    template <typename TC, typename W>
+    template <typename TC, typename W, bool U = UNITS<TC>>
     __host__ __device__ static void zT(const BasisT<TC> &Bs, const TC *A, const TC *SY, TC *SZ, const W &write,
                                        TC &out0, int tid)
     {
+        if constexpr (U) {
+            // one output node a of a line per unit (A's y-seams folded in by foldy), unit
+            // u = L + SE SE (a + D1 h), L = zx + SE zy; node 0 of segment h > 0 goes to the plane
+            // S0 = SZ + NSZ for seam()
+            constexpr int NU = SE * SE * D1 * TT, NR = (NU + TS::CTHREADS - 1) / TS::CTHREADS;
+            TC *S0 = SZ + TS::NSZ;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int u = tid + i * TS::CTHREADS;
+                if (u < NU) {
+                    const int L = u % (SE * SE), w = u / (SE * SE), a = w % D1, h = w / D1;
+                    const int zx = L % SE, zy = L / SE;
+                    TC acc = TC(0);
+#pragma unroll
+                    for (int q = 0; q < Q1; ++q) acc += Bs.B[q * D1 + a] * A[zx + SE * (Q1 * h + q) + SA * zy];
+                    if (a > 0 && a < K) write((K * h + a) * SE * SE + L, acc);
+                    else if (a == 0) {
+                        if (h == 0) write(L, acc);
+                        else S0[(h - 1) * SE * SE + L] = acc;
+                    } else if (h == TT - 1) write((SE - 1) * SE * SE + L, acc);
+                    else SZ[h * SE * SE + L] = acc;
+                }
+            }
+            return;
+        }
         int L, h;
         if (!line<SE*SE>(tid, L, h)) return;
         const int zx = L % SE, zy = L / SE;
@@ -536,9 +615,19 @@ struct Colloc {
         out0 = out[0];
     }
 
-    template <typename TC, typename W>
+    template <typename TC, typename W, bool U = UNITS<TC>>
     __host__ __device__ static void seam(const TC *SZ, const W &write, TC out0, int tid)
     {
+        if constexpr (U) {
+            constexpr int NU = SE * SE * (TT - 1), NR = (NU + TS::CTHREADS - 1) / TS::CTHREADS;
+            const TC *S0 = SZ + TS::NSZ;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int u = tid + i * TS::CTHREADS;
+                if (u < NU) write((K * (u / (SE * SE) + 1)) * SE * SE + u % (SE * SE), SZ[u] + S0[u]);
+            }
+            return;
+        }
         int L, h;
         if (!line<SE * SE>(tid, L, h) || h == 0) return;
         write((K * h * SE + L / SE) * SE + L % SE, SZ[(h - 1) * SE * SE + L] + out0);
@@ -659,8 +748,16 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::CTHREADS, tile_min_blocks<T
     __syncthreads();
     S::x3(Bs, fx, FY, FZ, C, SX, tid);
     __syncthreads();
+    if constexpr (S::template UNITS<TC>) {
+        S::foldx(C, SX, tid);
+        __syncthreads();
+    }
     S::yT(Bs, C, SX, A, SY, tid);
     __syncthreads();
+    if constexpr (S::template UNITS<TC>) {
+        S::foldy(A, SY, tid);
+        __syncthreads();
+    }
     S::zT(Bs, A, SY, SZ, write, out0, tid);
     __syncthreads();
     S::seam(SZ, write, out0, tid);

@@ -188,15 +188,27 @@ __global__ void __launch_bounds__(TileShape<D1, TT>::CTHREADS, tile_min_blocks<T
     res_x2<D1, TT, TAN>(P, Bs, t, U, fx, sv, FY, FZ, T64, T32, tid);
     if constexpr (RES) {
         __syncthreads();
+        // the transposed stages on work units (seams folded in first), except at order 5, where
+        // their registers cost this kernel more than the idle lanes they save (2.46 -> 2.63 ms
+        // at 8M DOFs; orders 1-4 and 6 gained 1-6 %)
+        constexpr bool TU = D1 != 6;
         S::template x3s<double, true>(Bs, fx, sv, FY, FZ, C, SX, tid);
         __syncthreads();
-        S::yT(Bs, C, SX, A, SY, tid);
+        if constexpr (TU) {
+            S::foldx(C, SX, tid);
+            __syncthreads();
+        }
+        S::template yT<double, TU>(Bs, C, SX, A, SY, tid);
         __syncthreads();
+        if constexpr (TU) {
+            S::foldy(A, SY, tid);
+            __syncthreads();
+        }
         const ResWriter write{ codes, hd, r, halo };
         double out0 = 0.0;
-        S::zT(Bs, A, SY, SZ, write, out0, tid);
+        S::template zT<double, ResWriter, TU>(Bs, A, SY, SZ, write, out0, tid);
         __syncthreads();
-        S::seam(SZ, write, out0, tid);
+        S::template seam<double, ResWriter, TU>(SZ, write, out0, tid);
     }
 }
 

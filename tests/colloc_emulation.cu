@@ -85,7 +85,9 @@ double run(unsigned seed, bool reverse)
     each([&](int t) { S::x1(Bs, C, Uq, t); });
     each([&](int t) { S::x2(Bs, Tbs, Uq, fxs.data() + (size_t)t * Q1, FY, FZ, t); });
     each([&](int t) { S::x3(Bs, fxs.data() + (size_t)t * Q1, FY, FZ, C, SX, t); });
+    if constexpr (S::template UNITS<double>) each([&](int t) { S::foldx(C, SX, t); });
     each([&](int t) { S::yT(Bs, C, SX, A, SY, t); });
+    if constexpr (S::template UNITS<double>) each([&](int t) { S::foldy(A, SY, t); });
     each([&](int t) { S::zT(Bs, A, SY, SZ, write, out0[t], t); });
     each([&](int t) { S::seam(SZ, write, out0[t], t); });
     // reference: per element, full tensor products
