@@ -164,9 +164,11 @@ fe_status fe_jacobian_action(fe_ctx *ctx, const double *u, const void *v, void *
 /* Same as fe_jacobian_action with u == NULL but v_host/y_host are HOST buffers (pinned memory
  * recommended): copies v to the device, applies J, copies y back; synchronises `stream` before
  * returning.  For 3D problems whose tile kernel has several tile layers along z, the action runs
- * in up to 8 z-chunks: each chunk's DOF planes are copied in on a copy stream while earlier
- * chunks compute, and the planes that are complete are copied back on another while later
- * chunks compute (the same kernels and sums as the one-piece action: the same bits). */
+ * in z-chunks (32 for precision 64 and 8 otherwise, at most one per tile layer): each chunk's
+ * DOF planes are copied in on a copy stream while earlier chunks compute, and the planes that are
+ * complete are copied back on another while later chunks compute (the same kernels and sums as
+ * the one-piece action: the same bits).  The call uses internal streams of its own, the chunks'
+ * fix-ups on one of the device's highest priority. */
 fe_status fe_jacobian_action_host(fe_ctx *ctx, const void *v_host, void *y_host, int precision,
                                   void *stream);
 
