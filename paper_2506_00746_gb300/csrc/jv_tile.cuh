@@ -136,7 +136,8 @@ __device__ __forceinline__ void lds_run(const TC *p, TC (&r)[N])
 //   x3 (line (qy, qz)):                      W = Dc_x^T FX + Dc_y^T FY + Dc_z^T FZ, C = B_x^T W
 //   yT (line (sx, qz)):                      A = B_y^T C
 //   zT (line (sx, sy)):                      out = B_z^T A, written through the slot codes
-// with seam planes for the DOFs that neighbouring segments share (left term first).  The point
+// with seam planes for the DOFs that neighbouring segments share (left term first).  In FP64 the
+// z, y, yT and zT stages take one output of a line per thread instead of a line (UNITS).  The point
 // arrays U, FX, FY, FZ are indexed (qx, qy, qz) -> qz + QT (qy + QT qx).  The functions are host-
 // callable so that a host loop over the thread indices can run them between the same barriers.
 template <int D1, int TT>
@@ -239,12 +240,13 @@ struct Colloc {
             for (int a = 0; a < D1; ++a) out[a] += Bs.B[q * D1 + a] * in[q];
     }
 
-    // FP64 z and y stages: one output point of a line per work unit (each sum still over a
-    // ascending), the units of all segments on consecutive threads in rounds of CTHREADS.  With one
+    // FP64 z, y, yT and zT stages: one output of a line per work unit (each sum in its original
+    // order), the units of all segments on consecutive threads in rounds of CTHREADS.  With one
     // line per thread the last warp of a segment's lines runs its Q1 D1 multiply-adds for a few
     // lanes (order 3: 49 z-lines of a segment in two warps); FP64 instructions cost their full
-    // issue whatever the lanes, so the units waste fewer (order 3: 52 + 56 instead of 64 + 64 FP64
-    // warp-instructions per tile for the 49 + 56 of useful work).
+    // issue whatever the lanes, so the units waste fewer (order 3: 52 + 56 + 56 + 52 instead of
+    // 4 x 64 FP64 warp-instructions per tile for 49 + 56 + 56 + 49 of useful work).  The seam terms
+    // of yT and zT are folded in beforehand (foldx, foldy).
     template <typename TC>
     static constexpr bool UNITS = std::is_same<TC, double>::value;
 
